@@ -1,0 +1,145 @@
+"""Pins of the oracle's full HALLaR solve (Alg. 1 with ADAP-AIPP / ADAP-FISTA)
+against SDP values known in closed form, and its certificates.
+
+Closed forms:
+* Max-Cut SDP of K_n = n^2/4; of a bipartite graph with nonnegative weights
+  = total weight; of the odd cycle C_n = (n/2)(1 + cos(pi/n)).
+* Lovasz theta: theta(C_n) = n cos(pi/n)/(1 + cos(pi/n)) for odd n;
+  theta(K_n) = 1; theta of the empty graph = n (optimal X = 11^T/n);
+  theta(Q_d) = 2^(d-1) (Q_d is bipartite, hence perfect, eq. lovasz remark).
+* Matrix completion (eq. matcomp-sdp): with enough samples the optimum is
+  ||M||_* and the off-diagonal block of X is M.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hallar_oracle as O
+from paper_2505_13719_b300 import instances as I
+from tests.test_oracle_operators import dense_As, dense_C
+
+TOL = 1e-7
+
+
+def solve(inst, r0=2, seed=7, **kw):
+    opt = O.Options(tol=TOL, **kw)
+    return O.hallar_solve(inst, I.initial_factor(inst.n, r0, seed), opt=opt)
+
+
+def check_certificate(inst, res):
+    # S = C + A*p + theta I psd (eq. St) by dense eigendecomposition, and
+    # the relative KKT residuals of eq. termination2 below the tolerance
+    S = dense_C(inst) + sum(q * A for q, A in zip(res.p, dense_As(inst))) + res.theta * np.eye(inst.n)
+    lam = np.linalg.eigvalsh(S)[0]
+    assert lam >= -1e-5 * (1 + np.abs(dense_C(inst)).sum(axis=0).max())
+    assert res.converged and res.kkt <= TOL
+    assert np.linalg.norm(res.U) <= math.sqrt(inst.tau2) * (1 + 1e-12)
+
+
+CASES = [
+    ("maxcut K8", lambda: I.maxcut(8, *I.complete_graph(8)), 16.0),
+    ("maxcut C5", lambda: I.maxcut(5, *I.cycle_graph(5)), 2.5 * (1 + math.cos(math.pi / 5))),
+    ("maxcut C7", lambda: I.maxcut(7, *I.cycle_graph(7)), 3.5 * (1 + math.cos(math.pi / 7))),
+    ("maxcut C6", lambda: I.maxcut(6, *I.cycle_graph(6)), 6.0),
+    ("maxcut torus 4x4", lambda: I.maxcut(16, *I.torus_graph(4, 4)), 32.0),
+    ("maxcut weighted bipartite", lambda: _weighted_bipartite(), None),
+    ("theta C5", lambda: I.theta(5, *I.cycle_graph(5)), math.sqrt(5.0)),
+    ("theta C7", lambda: I.theta(7, *I.cycle_graph(7)),
+     7 * math.cos(math.pi / 7) / (1 + math.cos(math.pi / 7))),
+    ("theta K6", lambda: I.theta(6, *I.complete_graph(6)), 1.0),
+    ("theta empty 6", lambda: I.theta(6, np.zeros(0, int), np.zeros(0, int)), 6.0),
+    ("theta Q4", lambda: I.theta(16, *I.hypercube_graph(4)), 8.0),
+    ("theta C5 no trace row", lambda: I.theta(5, *I.cycle_graph(5), trace_row=False), math.sqrt(5.0)),
+]
+
+
+def _weighted_bipartite():
+    rng = np.random.default_rng(3)
+    a, b = 5, 6
+    ei, ej, w = [], [], []
+    for i in range(a):
+        for j in range(b):
+            if rng.random() < 0.6:
+                ei.append(i)
+                ej.append(a + j)
+                w.append(rng.uniform(0.5, 2.0))
+    inst = I.maxcut(a + b, ei, ej, w)
+    inst.meta["ref"] = float(np.sum(w))
+    return inst
+
+
+@pytest.mark.parametrize("name,make,ref", CASES, ids=[c[0] for c in CASES])
+def test_closed_form_values(name, make, ref):
+    inst = make()
+    if ref is None:
+        ref = inst.meta["ref"]
+    res = solve(inst)
+    assert abs(res.user_value - ref) <= 1e-5 * abs(ref), (res.user_value, ref)
+    check_certificate(inst, res)
+
+
+def test_empty_graph_theta_solution_is_unique():
+    # theta of the empty graph: X = 11^T / n is the unique optimum
+    n = 6
+    inst = I.theta(n, np.zeros(0, int), np.zeros(0, int))
+    res = solve(inst)
+    X = res.U @ res.U.T
+    np.testing.assert_allclose(X, np.ones((n, n)) / n, atol=1e-4)
+
+
+def test_matrix_completion_recovers_nuclear_norm():
+    inst = I.completion(10, 12, 2, 100, seed=5)
+    res = solve(inst)
+    nuc = inst.meta["nuclear_norm"]
+    assert abs(res.user_value - nuc) <= 1e-4 * nuc
+    X = res.U @ res.U.T
+    M = inst.meta["G"] @ inst.meta["H"].T
+    assert np.linalg.norm(X[:10, 10:] - M) <= 1e-3 * np.linalg.norm(M)
+    check_certificate(inst, res)
+
+
+def test_weak_duality_and_gap():
+    inst = I.maxcut(12, *I.er_graph(12, 0.5, 9))
+    res = solve(inst)
+    # dval <= P* <= pval up to the tolerance; the closed form is unknown here,
+    # so check the pair against each other and against a dense eigenvalue
+    assert res.dval <= res.pval + 1e-6 * (1 + abs(res.pval))
+    assert abs(res.pval - res.dval) <= 2e-7 * (1 + abs(res.pval) + abs(res.dval))
+    check_certificate(inst, res)
+
+
+def test_aipp_output_invariants():
+    # ADAP-AIPP returns R in grad g(W) + N_B(W), |R| <= rho, g(W) <= g(W0)
+    inst = I.maxcut(20, *I.er_graph(20, 0.3, 2))
+    rng = np.random.default_rng(1)
+    U0 = O.project_ball(rng.standard_normal((20, 3)), math.sqrt(inst.tau2))
+    p = rng.standard_normal(inst.m) * 0.1
+    beta = 2.0
+    cnt = O.Counters()
+    sub = O._Subproblem(inst, p, beta, cnt)
+    st = O.AippState(lam=1.0)
+    rho = 1e-4
+    tau = math.sqrt(inst.tau2)
+    W, R = O.adap_aipp(sub, U0, rho, st, O.Options(), tau)
+    assert np.linalg.norm(R) <= rho
+    assert O.al_value(inst, W, p, beta) <= O.al_value(inst, U0, p, beta)
+    grad = 2.0 * O.al_grad(inst, W, p, beta).W
+    N = R - grad
+    nrmW = np.linalg.norm(W)
+    assert nrmW <= tau * (1 + 1e-12)
+    if nrmW < tau * (1 - 1e-9):
+        assert np.linalg.norm(N) <= 1e-8 * (1 + np.linalg.norm(grad))
+    else:
+        c = float(np.sum(N * W)) / nrmW ** 2
+        assert c >= -1e-8
+        assert np.linalg.norm(N - c * W) <= 1e-8 * (1 + np.linalg.norm(grad))
+
+
+def test_rank_trim_keeps_leading_subspace():
+    rng = np.random.default_rng(0)
+    Y = rng.standard_normal((30, 6)) @ np.diag([5, 4, 3, 2, 1e-3, 1e-4])
+    Yt = O.trim_rank(Y, 4)
+    X, Xt = Y @ Y.T, Yt @ Yt.T
+    assert Yt.shape == (30, 4)
+    assert np.linalg.norm(X - Xt) <= 1e-2 * np.linalg.norm(X)
