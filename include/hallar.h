@@ -1,0 +1,209 @@
+/*
+ * hallar.h -- C ABI of the B300 (sm_103a) HALLaR hot-path library.
+ *
+ * HALLaR (the hybrid low-rank augmented Lagrangian method) solves
+ *
+ *   (P)  min C.X  s.t.  A(X) = b,  X psd,  tr X <= tau^2          (Section 1, eq. P)
+ *
+ * through the factorisation X = UU^T, U in R^{n x r}.  Its data-parallel hot
+ * path is a handful of operator evaluations on U (Section 4):
+ *
+ *   T  = A~(UU^T) = [C.UU^T ; A_1.UU^T ; ... ; A_m.UU^T]   (eq. A tilde operator)
+ *   p' = p + beta (A(UU^T) - b)                            (eq. Grad U Space)
+ *   W  = (C + A*(p')) U,   grad_U L_beta(UU^T; p) = 2W      (eqs. Grad U Space,
+ *                                                            Adjoint calculation)
+ *   lambda_min, v_min of G = C + A*(p')                     (Alg. 1 step 7)
+ *
+ * and the HALLaR loop (Alg. 1, ADAP-AIPP / ADAP-FISTA of Appendix A) that
+ * drives them to a relative KKT tolerance (eq. termination2).
+ *
+ * Problem data.  C = C_sparse + C_J * 11^T + C_I * I, with C_sparse a
+ * symmetric matrix in full CSR (both triangles; the diagonal may be stored).
+ * The constraint family fixes the A_l:
+ *   HALLAR_DIAG      A_i = e_i e_i^T, i = 0..n-1 (m = n).  Max-Cut SDP.
+ *   HALLAR_EDGE      A_l = (e_i e_j^T + e_j e_i^T)/2 for pair l = (i, j), i != j,
+ *                    so A_l.X = X_ij; optionally followed by a trace row A = I.
+ *                    Lovasz theta SDP (eq. lovasz).
+ *   HALLAR_OBSERVED  the EDGE family on pairs (i, n1 + j), i < n1, j < n - n1.
+ *                    Matrix completion SDP (eq. matcomp-sdp).
+ * Constraint l of the pair list is row l of b / p / residuals; the trace row,
+ * when present, is the last one.  T has m + 1 entries, T[0] = C.UU^T.
+ *
+ * Memory and pointers.  A handle owns every device buffer it allocates and
+ * frees them in hallar_destroy.  Arguments of hallar_create are HOST arrays,
+ * copied to the device once (Section 3.1: data resident on the GPU).  Every
+ * array argument of the other calls may be a host or a device pointer: the
+ * library asks the CUDA runtime which it is and stages host arrays through
+ * its own device buffers.  Factor arrays (U, W) are row-major n x r with
+ * leading dimension r and hold double for HALLAR_FP64 handles and float for
+ * HALLAR_MIXED handles; every other floating array is double.  Work is
+ * issued on the handle's stream (hallar_options.stream, NULL = a stream the
+ * handle creates); calls return after their results are complete.
+ *
+ * Errors.  Every call returns a hallar_status and never aborts, traps or
+ * exits; hallar_last_error(h) describes the last failure on h.  Input
+ * validation (indices in range, C symmetric, finite values, sizes) happens
+ * on the host before any kernel runs.  Kernels never spin on a flag.
+ *
+ * Precision.  HALLAR_FP64 keeps every quantity in double.  HALLAR_MIXED keeps
+ * U, the row dot products and the SpMM in float with float accumulation; the
+ * multipliers p, the residuals r, p', the reductions (C.UU^T, p^T r,
+ * ||r||^2), Lanczos (basis, orthogonalisation, Ritz values), the dual update,
+ * the KKT norms and the Frank-Wolfe and line-search scalars stay in double.
+ *
+ * Limits.  n < 2^31, stored nonzeros < 2^31, r <= 256; hallar_solve takes
+ * r_cap <= 89 (its rank trim diagonalises an (r_cap+1)^2 Gram matrix).
+ */
+#ifndef HALLAR_H
+#define HALLAR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hallar_ctx* hallar_t;
+
+typedef enum {
+  HALLAR_OK = 0,
+  HALLAR_EINVAL = 1,    /* bad argument: null pointer, size or index out of
+                           range, non-finite value, asymmetric C            */
+  HALLAR_ENOMEM = 2,    /* device allocation failed                        */
+  HALLAR_ECUDA = 3,     /* CUDA runtime error (message in last_error)      */
+  HALLAR_ENOTCONV = 4,  /* iteration limit reached before the tolerance    */
+  HALLAR_ETIMEOUT = 5,  /* wall-clock limit reached before the tolerance   */
+  HALLAR_ERANK = 6,     /* rank would exceed the cap and trimming failed   */
+  HALLAR_ENUMERIC = 7   /* a NaN or Inf appeared in a reduction            */
+} hallar_status;
+
+typedef enum { HALLAR_DIAG = 0, HALLAR_EDGE = 1, HALLAR_OBSERVED = 2 } hallar_family;
+typedef enum { HALLAR_FP64 = 0, HALLAR_MIXED = 1 } hallar_precision;
+
+/* Parameters of the method.  The paper fixes none of sigma, chi, lambda_0,
+ * beta_0 or the epsilon_t / beta_t schedules (Alg. 1 remarks, Appendix A);
+ * hallar_default_options fills this library's choices. */
+typedef struct {
+  double tol;             /* relative KKT tolerance of eq. termination2 (1e-5)    */
+  double sigma;           /* ADAP-FISTA success parameter sigma (0.3)             */
+  double chi;             /* ADAP-FISTA parameter chi in (0,1) (0.5)              */
+  double lambda0;         /* initial ADAP-AIPP prox stepsize (1)                  */
+  double beta0;           /* initial penalty beta_1 (1)                           */
+  double beta_max;        /* cap of the penalty schedule (1e8)                    */
+  double eps_decay;       /* epsilon_{t+1} = eps_decay * epsilon_t (0.5)          */
+  double eps1_rel;        /* epsilon_1 = eps1_rel (1 + tau^2 ||C||_1) (1e-2)      */
+  double lanczos_tol_rel; /* Ritz residual tolerance = this * epsilon_t / tau^2   */
+  double time_limit_s;    /* wall-clock limit of hallar_solve (3600)              */
+  int32_t r_cap;          /* maximum factor rank; the Gram trim keeps r_cap (32)  */
+  int32_t max_outer;      /* AL iterations (300)                                  */
+  int32_t max_hlr;        /* HLR iterations per AL iteration (100)                */
+  int32_t max_aipp;       /* ADAP-AIPP iterations per call (20000)                */
+  int32_t max_fista;      /* ADAP-FISTA iterations per call (400)                 */
+  int32_t lanczos_kmax;   /* Lanczos basis size before a restart (300)            */
+  int32_t precision;      /* hallar_precision                                     */
+  int32_t verbose;        /* 1: one line per AL iteration on stderr               */
+  uint64_t seed;          /* seed of the Lanczos start vectors (SplitMix64)       */
+  void* stream;           /* cudaStream_t to issue on; NULL: the handle's own     */
+} hallar_options;
+
+/* Counters and results of hallar_solve.  pval = C.UU^T, dval = -b^T p -
+ * tau^2 theta, and the three relative residuals of eq. termination2. */
+typedef struct {
+  double pval, dval, theta, lam_min_S;
+  double rel_primal, rel_gap, rel_dual, kkt;
+  double beta, seconds;
+  int32_t rank, converged;
+  int32_t outer_iters, hlr_iters, aipp_iters, fista_iters, fista_failures;
+  int32_t lanczos_iters, fw_steps, trims;
+  int64_t grad_evals, value_evals, kernel_launches;
+} hallar_result;
+
+/* Fill *opt with the defaults listed above.  HALLAR_EINVAL for opt == NULL. */
+hallar_status hallar_default_options(hallar_options* opt);
+
+/* Build a problem on the current CUDA device (Section 3.1: C, A and b are
+ * copied to the GPU once and stay resident).
+ *   n              order of X (> 0).
+ *   n1             HALLAR_OBSERVED only: rows of the observed block; else 0.
+ *   C_rowptr[n+1], C_col[nnz], C_val[nnz]: symmetric sparse part of C in
+ *                  full CSR (host); C_rowptr NULL means an empty sparse part.
+ *   C_J, C_I       implicit C_J 11^T + C_I I added to C.
+ *   family         hallar_family.
+ *   m_pairs        EDGE / OBSERVED: number of pairs; DIAG: must be 0.
+ *   cons_i, cons_j [m_pairs] pair indices (host).
+ *   has_trace_row  EDGE / OBSERVED: 1 adds the constraint tr X = b[m-1].
+ *   b              [m] right-hand side (host), m = n (DIAG) or
+ *                  m_pairs + has_trace_row.
+ *   tau2           tau^2 > 0, the trace bound of the spectraplex.
+ *   opt            NULL for defaults; copied.
+ *   out            receives the handle (NULL on failure).
+ * Errors: HALLAR_EINVAL (validation), HALLAR_ENOMEM, HALLAR_ECUDA. */
+hallar_status hallar_create(int64_t n, int64_t n1,
+                            const int64_t* C_rowptr, const int32_t* C_col,
+                            const double* C_val, double C_J, double C_I,
+                            int32_t family, int64_t m_pairs,
+                            const int32_t* cons_i, const int32_t* cons_j,
+                            int32_t has_trace_row, const double* b, double tau2,
+                            const hallar_options* opt, hallar_t* out);
+
+/* T = A~(UU^T) (eq. A tilde operator; the sum of Alg. 2 / Alg. 3).
+ *   U  [n x r] factor (host or device), r in [1, 256].
+ *   T  [m + 1] doubles (host or device): T[0] = C.UU^T, T[1+l] = A_l.UU^T. */
+hallar_status hallar_eval_A(hallar_t h, const void* U, int32_t r, double* T);
+
+/* One fused gradient evaluation (eqs. AL function, Grad U Space, Adjoint
+ * calculation): with r_l = A_l.UU^T - b_l and p' = p + beta r,
+ *   W     [n x r] = (C + A*(p')) U   (the U-gradient of L_beta is 2W),
+ *   g_val [1]     = C.UU^T + p^T r + beta/2 ||r||^2   (host; may be NULL),
+ *   resid [m]     = r                                  (may be NULL).
+ * p is [m] doubles.  U and W must not overlap. */
+hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
+                          double beta, void* W, double* g_val, double* resid);
+
+/* Minimum eigenpair of G = C + A*(p') (Alg. 1 step 7, eq. Grad X Space) by
+ * Lanczos with full reorthogonalisation, restarted from the Ritz vector
+ * every kmax steps, until ||G v - lambda v|| <= tol or 50 restarts.
+ *   pshift [m]  p' (doubles).
+ *   v0     [n]  start vector, or NULL for the SplitMix64 vector of opt.seed.
+ *   lambda_min (host), v [n] (unit), iters (host), resid (host): outputs;
+ *   v, iters, resid may be NULL.
+ * Returns HALLAR_ENOTCONV (with the best Ritz pair written) when the
+ * tolerance was not met. */
+hallar_status hallar_min_eig(hallar_t h, const double* pshift, double tol,
+                             int32_t kmax, const double* v0, double* lambda_min,
+                             double* v, int32_t* iters, double* resid);
+
+/* Run HALLaR (Alg. 1) from U0 [n x r0] (projected onto the ball ||U||_F <= tau
+ * when outside it) and p0 [m] (NULL = 0) to the relative KKT tolerance of
+ * eq. termination2.  The final factor and multipliers stay on the device;
+ * read them with hallar_get_solution.  res (host) may be NULL.
+ * Returns HALLAR_OK on convergence, HALLAR_ENOTCONV / HALLAR_ETIMEOUT when a
+ * limit was hit first (res still filled). */
+hallar_status hallar_solve(hallar_t h, const void* U0, int32_t r0, const double* p0,
+                           hallar_result* res);
+
+/* Copy the last solve's factor U [n x rank] (leading dimension rank; needs
+ * r_capacity >= rank) and multipliers p [m] out (host or device).  U and p
+ * may be NULL; rank (host) receives the rank when non-NULL. */
+hallar_status hallar_get_solution(hallar_t h, void* U, int32_t r_capacity, double* p,
+                                  int32_t* rank);
+
+/* Problem sizes of a handle (host pointers; any may be NULL). */
+hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz_merged,
+                               int32_t* precision);
+
+/* Free every resource of h (NULL is a no-op). */
+void hallar_destroy(hallar_t h);
+
+/* Message of the last failure on h ("" if none); for h == NULL, the last
+ * failure of hallar_create on this thread.  Valid until the next call on h. */
+const char* hallar_last_error(hallar_t h);
+
+/* Name of a status code. */
+const char* hallar_status_string(hallar_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HALLAR_H */

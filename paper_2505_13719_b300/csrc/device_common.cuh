@@ -1,0 +1,121 @@
+// Device helpers shared by the kernels: 16-byte vector access to factor rows,
+// group shuffles and the deterministic block -> grid reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hallar {
+
+constexpr int kBlock = 256;  // threads per block of every row kernel
+
+// 16-byte vectors of the factor element type -------------------------------
+template <class T> struct V16;
+template <> struct V16<double> {
+  using type = double2;
+  static constexpr int N = 2;
+  __device__ static inline void unpack(const double2& v, double* o) { o[0] = v.x; o[1] = v.y; }
+  __device__ static inline double2 pack(const double* o) { return make_double2(o[0], o[1]); }
+};
+template <> struct V16<float> {
+  using type = float4;
+  static constexpr int N = 4;
+  __device__ static inline void unpack(const float4& v, float* o) {
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+  __device__ static inline float4 pack(const float* o) { return make_float4(o[0], o[1], o[2], o[3]); }
+};
+
+template <class T>
+__device__ inline void load_chunk(const T* __restrict__ base, int64_t off, T* o) {
+  using VT = typename V16<T>::type;
+  VT v = __ldg(reinterpret_cast<const VT*>(base + off));
+  V16<T>::unpack(v, o);
+}
+template <class T>
+__device__ inline void load_chunk_l2(const T* __restrict__ base, int64_t off, T* o) {
+  // gathered neighbour rows: served from L2, no L1 allocation
+  using VT = typename V16<T>::type;
+  VT v = __ldcg(reinterpret_cast<const VT*>(base + off));
+  V16<T>::unpack(v, o);
+}
+template <class T>
+__device__ inline void store_chunk(T* base, int64_t off, const T* o) {
+  using VT = typename V16<T>::type;
+  *reinterpret_cast<VT*>(base + off) = V16<T>::pack(o);
+}
+
+// sum over the G lanes of a group (G a power of two, groups aligned) -------
+template <int G, class T>
+__device__ inline T group_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, G);
+  return v;
+}
+template <int G>
+__device__ inline unsigned group_mask() {
+  if (G == 32) return 0xffffffffu;
+  unsigned lane = threadIdx.x & 31u;
+  unsigned base = lane & ~(unsigned)(G - 1);
+  return ((1u << (G & 31)) - 1u) << base;
+}
+
+// deterministic reduction of NS doubles over the grid ------------------------
+// Every block reduces its threads' values (fixed tree), writes one partial
+// per scalar, and the last block to finish sums the partials in block order
+// (fixed assignment of blocks to threads, then the same fixed tree), writes
+// out[0..NS) and re-arms the counter.  Results do not depend on scheduling.
+template <int NS>
+__device__ inline void block_sum(double (&v)[NS], double (*sh)[kBlock / 32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double x = v[s];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    if (lane == 0) sh[s][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) x += sh[s][w];
+      v[s] = x;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NS>
+__device__ inline void grid_reduce(double (&v)[NS], double* __restrict__ partials,
+                                   unsigned* counter, double* out) {
+  __shared__ double sh[NS][kBlock / 32];
+  __shared__ bool am_last;
+  block_sum<NS>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) partials[(size_t)blockIdx.x * NS + s] = v[s];
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double acc[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) acc[s] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kBlock) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) acc[s] += __ldcg(&partials[(size_t)b * NS + s]);
+  }
+  block_sum<NS>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) out[s] = acc[s];
+    *counter = 0u;
+  }
+}
+
+}  // namespace hallar

@@ -1,0 +1,244 @@
+// Internal declarations of the HALLaR sm_103a library: the problem layout in
+// HBM, the handle, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hallar.h"
+
+namespace hallar {
+
+// ---------------------------------------------------------------------------
+// layout of a problem on the device
+// ---------------------------------------------------------------------------
+// The merged CSR holds, per row i, the off-diagonal entries of C and of the
+// constraint matrices (the merged support S of eq. support S ell and its
+// mirror, Section 4).  Per entry: the column (int32), for families with a
+// sparse C its value, and for pair families a constraint code:
+//   code >= 0        constraint l = code, this entry is the owner (the pair's
+//                    first index is this row); it writes r_l.
+//   code in [-m, -1] constraint l = -code - 1, mirrored entry.
+//   code == kNoCons  a pure C entry (value in cval).
+// The diagonal of C plus C_I sits in cdiag[n].
+enum Family : int { FAM_DIAG = 0, FAM_EDGE = 1, FAM_EDGE_C = 2 };
+constexpr int32_t kNoCons = INT32_MIN;
+
+struct Problem {
+  int fam = FAM_DIAG;       // kernel family
+  int api_family = 0;       // hallar_family as created
+  int64_t n = 0, n1 = 0, m = 0, m_pairs = 0, nnz = 0;
+  int has_trace = 0;
+  double C_J = 0.0, C_I = 0.0, tau2 = 1.0;
+  double b_norm1 = 0.0, c_norm1 = 0.0;
+  int* rowptr = nullptr;    // [n+1]
+  int* col = nullptr;       // [nnz]
+  int* code = nullptr;      // [nnz] (pair families)
+  double* cval = nullptr;   // [nnz] (families with sparse C)
+  float* cval32 = nullptr;  // float copy for the mixed form
+  double* cdiag = nullptr;  // [n]
+  double* b = nullptr;      // [m]
+};
+
+// ---------------------------------------------------------------------------
+// reductions: per-block partials, summed by the last block in a fixed order
+// ---------------------------------------------------------------------------
+constexpr int kMaxRed = 16;      // scalars per grid reduction
+constexpr int kMaxBlocks = 4096; // largest reduction grid
+constexpr int kColsumMax = 256;  // column-sum buffers hold up to 256 columns
+
+struct RedBuf {
+  double* partials = nullptr;   // [kMaxBlocks * (2 kColsumMax + 2)]
+  unsigned* counter = nullptr;
+};
+
+// device scalar slots (doubles), mirrored to pinned host memory
+enum Slot : int {
+  S_GRAD = 0,    // fused operator: C.UU^T part, p.r, r.r
+  S_PRE = 8,     // pre-pass: |U|_F^2, |colsum|^2
+  S_DIFF = 16,   // value change: dT0, p.dT, dT(2rX+dT), trace dT; [4..5] colsum pass
+  S_VEC = 32,    // streaming kernels
+  S_VEC2 = 48,   // streaming kernels (second set)
+  S_LAN = 64,    // Lanczos
+  S_SCALE = 80,  // |z|^2 and host->device scalar staging
+  S_COUNT = 96
+};
+
+}  // namespace hallar
+
+// the opaque handle of hallar.h
+struct hallar_ctx {
+  hallar::Problem P;
+  hallar_options opt;
+  int device = 0;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  hallar::RedBuf red;
+  double* d_scal = nullptr;     // [S_COUNT]
+  double* h_scal = nullptr;     // pinned mirror
+  double* d_colsum = nullptr;   // [4 * kColsumMax]
+  std::string last_error;
+  int64_t launches = 0;
+  // every device buffer the handle owns
+  std::vector<void*> owned;
+  // staging buffers of the operator entry points (grown on demand)
+  void* stage_u = nullptr; size_t stage_u_bytes = 0;
+  void* stage_w = nullptr; size_t stage_w_bytes = 0;
+  void* stage_wout = nullptr; size_t stage_wout_bytes = 0;
+  double* stage_m0 = nullptr; size_t stage_m0_bytes = 0;
+  double* stage_m1 = nullptr; size_t stage_m1_bytes = 0;
+  double* stage_p0 = nullptr; size_t stage_p0_bytes = 0;
+  void* eig_stage = nullptr; size_t eig_stage_bytes = 0;
+  void* gram_part = nullptr; size_t gram_part_bytes = 0;
+  // Lanczos workspace (basis, vectors, partial rows)
+  void* lan_Q = nullptr; size_t lan_Q_bytes = 0;
+  void* lan_w = nullptr; size_t lan_w_bytes = 0;
+  void* lan_part = nullptr; size_t lan_part_bytes = 0;
+  void* lan_h = nullptr; size_t lan_h_bytes = 0;
+  // buffers of the last solve (freed by the next solve or by destroy)
+  std::vector<void*> solve_bufs;
+  void* sol_U = nullptr; int sol_rank = 0; int sol_ld = 0;
+  double* sol_p = nullptr;
+};
+
+namespace hallar {
+using Ctx = ::hallar_ctx;
+
+// error helpers -------------------------------------------------------------
+struct Err {
+  hallar_status st;
+  std::string msg;
+};
+
+#define HL_CUDA(call)                                                             \
+  do {                                                                            \
+    cudaError_t e__ = (call);                                                     \
+    if (e__ != cudaSuccess)                                                       \
+      throw ::hallar::Err{e__ == cudaErrorMemoryAllocation ? HALLAR_ENOMEM          \
+                                                           : HALLAR_ECUDA,        \
+                          std::string(#call) + ": " + cudaGetErrorString(e__)};   \
+  } while (0)
+
+#define HL_CHECK_LAUNCH(ctx)                                                      \
+  do {                                                                            \
+    (ctx)->launches++;                                                            \
+    cudaError_t e__ = cudaGetLastError();                                         \
+    if (e__ != cudaSuccess)                                                       \
+      throw ::hallar::Err{HALLAR_ECUDA, std::string("kernel launch: ") +          \
+                                           cudaGetErrorString(e__)};              \
+  } while (0)
+
+inline void fail(hallar_status st, const std::string& m) { throw Err{st, m}; }
+
+// buffers -------------------------------------------------------------------
+template <class T>
+T* dalloc(Ctx* c, size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  HL_CUDA(cudaMalloc(&p, count * sizeof(T)));
+  c->owned.push_back(p);
+  return static_cast<T*>(p);
+}
+void dfree(Ctx* c, void* p);
+// grow *buf to at least `bytes` (contents not kept)
+void* ensure_buffer(Ctx* c, void** buf, size_t* cur_bytes, size_t bytes);
+void sync(Ctx* c);
+void fetch_scalars(Ctx* c, int first, int count);  // d_scal -> h_scal, then sync
+
+// element size of a factor array for this handle
+inline size_t elem_size(const Ctx* c) {
+  return c->opt.precision == HALLAR_MIXED ? sizeof(float) : sizeof(double);
+}
+// leading dimension used internally: r rounded up to 16 bytes
+inline int padded_ld(const Ctx* c, int r) {
+  int v = c->opt.precision == HALLAR_MIXED ? 4 : 2;
+  return (r + v - 1) / v * v;
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (kernels_ops.cu / kernels_vec.cu / lanczos.cu)
+// ---------------------------------------------------------------------------
+struct GradOut {
+  void* W = nullptr;        // [n x ld] or null
+  double* resid = nullptr;  // [m] or null (owned constraints; the trace row is
+                            // written by the caller)
+  double* T = nullptr;      // [m+1] or null (T[0] and the trace row by the caller)
+};
+
+// pre-pass: colsum of U into colsum_out, S_PRE[0] = |U|_F^2, S_PRE[1] = |colsum|^2
+void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot);
+// fused A~(UU^T), shift and SpMM.  Reductions into S_GRAD:
+//   [0] C.UU^T without the C_J part, [1] sum p_l r_l, [2] sum r_l^2 (the
+//   trace row excluded).
+void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double beta,
+                 const double* colsum, GradOut out);
+// g(Y) - g(X) pieces into S_DIFF: [0] dT0 (no C_J part) [1] p.dT [2] dT(2rX+dT)
+// [3] trace dT = sum <D_i, Y_i + X_i>; rY (if non-null) = rX + dT.
+void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r,
+                         const double* p, const double* rX, double* rY);
+// colsum of D = Y - X and of Y + X (for the C_J part of a value change);
+// S_DIFF[4] = sum <D_i, Y_i + X_i>, S_DIFF[5] = <colsum D, colsum (Y + X)>
+void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD,
+                        double* sS);
+
+// r = 1 operator pieces in FP64 (Frank-Wolfe)
+void launch_fw_denom(Ctx* c, const double* y, const double* resid, double tau2, int slot);
+
+// streaming kernels (kernels_vec.cu); reductions into the given slot
+void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst, int r_copy,
+                     double scale_src);
+void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, double a,
+                     int ld);
+void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, double a,
+                    double tk, double tk_new, double L, int ld);
+void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,
+                    double lam, double L, int ld);
+void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* center,
+                    const void* W, double lam, double tau, int ld);
+void launch_aipp_check(Ctx* c, const void* Wy, const void* z, const void* y,
+                       const void* center, double lam, double L, int ld);
+void launch_scale(Ctx* c, void* U, int ld, double s);
+void launch_norm2(Ctx* c, const void* U, int ld, int slot);
+void launch_dot(Ctx* c, const void* W, const void* U, int ld, int slot);
+void launch_fw_append(Ctx* c, const void* Y, int ld, int r, const double* y, double sY,
+                      double sy, void* Ynew, int ld_new, int append);
+// m-length FP64 vectors: op 0: a = b + s cc; op 1: slot = <b, cc>; op 2: slot = |b|^2
+void launch_dvec(Ctx* c, int op, int64_t len, double* a, const double* b, const double* cc,
+                 double s, int slot);
+// Gram U^T U (r x r, FP64) and out = U Q (Q row-major r x k)
+void launch_gram(Ctx* c, const void* U, int ld, int r, double* G);
+void launch_right_mult(Ctx* c, const void* U, int ld, int r, const double* Q, int k, void* out,
+                       int ld_out);
+
+// Lanczos (lanczos.cu)
+struct LanczosOut {
+  double lambda;
+  double resid;
+  int iters;
+  bool converged;
+};
+LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, double tol, int kmax,
+                           int max_restarts, double* v_out);
+void launch_splitmix(Ctx* c, uint64_t seed, double* out, double mix_scale, const double* base);
+
+// solver (solver.cu)
+hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_result* res);
+
+// ---------------------------------------------------------------------------
+// grid sizing: a fixed grid per (work, items per block) so that reductions
+// are deterministic; at most 8 resident 256-thread blocks per SM.
+// ---------------------------------------------------------------------------
+inline int grid_for(const Ctx* c, int64_t work_items, int items_per_block) {
+  int64_t g = (work_items + items_per_block - 1) / items_per_block;
+  int64_t cap = (int64_t)c->num_sms * 8;
+  if (cap > kMaxBlocks) cap = kMaxBlocks;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace hallar

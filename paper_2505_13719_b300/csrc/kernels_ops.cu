@@ -1,0 +1,576 @@
+// Operator kernels of the HALLaR hot path on the n x r factor U.
+//
+// k_grad fuses, in one pass over the merged CSR, the constraint map
+// T = A~(UU^T) (Section 4.1, eq. A tilde operator; the sum Alg. 2 computes),
+// the multiplier shift p' = p + beta (A(UU^T) - b) and the SpMM
+// W = (C + A*(p'))U (Section 4.2, eq. Adjoint calculation; Alg. 4 forms M and
+// multiplies): each row gathers its neighbour rows once, forms the row dot
+// products it needs, shifts the multipliers in registers and accumulates W.
+// M is never stored.
+//
+// Thread mapping: a group of G lanes owns one row; lane l of the group holds
+// the 16-byte chunks l, l+G, ... of the row (K chunks), so every row access is
+// a 128-bit vector load and a group reads a 256-byte FP64 row (r = 32) with
+// one instruction per lane.  Gathered neighbour rows go through L2 (ld.cg):
+// the gather window of a row-ordered sweep is far smaller than the 126 MB L2.
+#include "device_common.cuh"
+#include "hallar_internal.cuh"
+
+namespace hallar {
+
+namespace {
+
+template <int FAM>
+struct FamTraits {
+  static constexpr bool kDiag = FAM == FAM_DIAG;
+  static constexpr bool kPairs = FAM != FAM_DIAG;
+  static constexpr bool kCval = FAM != FAM_EDGE;
+};
+
+struct OpArgs {
+  int64_t n;
+  int ld;
+  const int* __restrict__ rowptr;
+  const int* __restrict__ col;
+  const int* __restrict__ code;
+  const void* __restrict__ cval;      // element type of the factor
+  const double* __restrict__ cdiag;
+  const double* __restrict__ b;
+  const double* __restrict__ p;
+  double C_J;
+  double beta;
+  int has_trace;
+  int64_t trace_row;
+  double* partials;
+  unsigned* counter;
+  double* out;
+};
+
+// ---------------------------------------------------------------------------
+// fused constraint map + shift + SpMM
+// ---------------------------------------------------------------------------
+struct GradIO {
+  const void* __restrict__ U;
+  const double* __restrict__ colsum;  // [ld] or null: C_J 11^T U = 1 (colsum)^T
+  const double* __restrict__ pre;     // pre[0] = |U|_F^2 (trace row)
+  void* __restrict__ W;               // or null
+  double* __restrict__ resid;         // or null
+  double* __restrict__ Tout;          // T[1 + l] or null
+};
+
+template <class T, int FAM, int G, int K>
+__global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
+  using Tr = FamTraits<FAM>;
+  constexpr int VEC = V16<T>::N;
+  const T* __restrict__ U = static_cast<const T*>(io.U);
+  const T* __restrict__ cval = static_cast<const T*>(a.cval);
+  T* __restrict__ W = static_cast<T*>(io.W);
+  const int lane_g = threadIdx.x & (G - 1);
+  const unsigned gmask = group_mask<G>();
+  const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
+  const int nch = a.ld / VEC;
+
+  // shifted multiplier of the trace row, identical for every row
+  double ps_tr = 0.0;
+  if (Tr::kPairs && a.has_trace) {
+    const double rt = io.pre[0] - a.b[a.trace_row];
+    ps_tr = a.p[a.trace_row] + a.beta * rt;
+  }
+  // the C_J 11^T U term adds C_J * colsum to every row of W
+  T cj[K][VEC];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      const int c = (lane_g + k * G) * VEC + v;
+      cj[k][v] = (io.colsum != nullptr && c < a.ld) ? (T)(a.C_J * io.colsum[c]) : (T)0;
+    }
+
+  double red[3] = {0.0, 0.0, 0.0};  // C.UU^T (sparse + diagonal part), p.r, r.r
+  for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
+    T u[K][VEC], acc[K][VEC];
+    const int64_t rowoff = i * (int64_t)a.ld;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int ch = lane_g + k * G;
+      if (ch < nch) {
+        load_chunk<T>(U, rowoff + ch * VEC, u[k]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) u[k][v] = (T)0;
+      }
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[k][v] = (T)0;
+    }
+    T nrm_l = (T)0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) nrm_l = fma(u[k][v], u[k][v], nrm_l);
+    const T nrm = group_sum<G>(nrm_l, gmask);  // |U_i|^2
+
+    double dcoef = a.cdiag[i];
+    if (Tr::kDiag) {
+      // constraint i: A_i . UU^T = |U_i|^2
+      const double r = (double)nrm - a.b[i];
+      const double pi = a.p[i];
+      dcoef += pi + a.beta * r;
+      if (lane_g == 0) {
+        red[1] += pi * r;
+        red[2] += r * r;
+        if (io.resid) io.resid[i] = r;
+        if (io.Tout) io.Tout[i] = (double)nrm;
+      }
+    }
+    if (Tr::kPairs) dcoef += ps_tr;
+
+    const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
+    T cdot_l = (T)0;  // lane part of <U_i, sum_j C_ij U_j> over the C entries
+#pragma unroll 2
+    for (int e = e0; e < e1; ++e) {
+      const int64_t j = a.col[e];
+      T uj[K][VEC];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int ch = lane_g + k * G;
+        if (ch < nch) {
+          load_chunk_l2<T>(U, j * a.ld + ch * VEC, uj[k]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) uj[k][v] = (T)0;
+        }
+      }
+      T coef;
+      bool is_c;
+      if (Tr::kDiag) {
+        coef = cval[e];
+        is_c = true;
+      } else {
+        const int cd = a.code[e];
+        is_c = Tr::kCval && cd == kNoCons;
+        if (is_c) {
+          coef = cval[e];
+        } else {
+          // pair constraint l: A_l . UU^T = <U_i, U_j>
+          T d_l = (T)0;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) d_l = fma(u[k][v], uj[k][v], d_l);
+          const T dot = group_sum<G>(d_l, gmask);
+          const bool owner = cd >= 0;
+          const int l = owner ? cd : -cd - 1;
+          const double r = (double)dot - a.b[l];
+          const double pl = a.p[l];
+          coef = (T)(0.5 * (pl + a.beta * r));
+          if (owner && lane_g == 0) {
+            red[1] += pl * r;
+            red[2] += r * r;
+            if (io.resid) io.resid[l] = r;
+            if (io.Tout) io.Tout[l] = (double)dot;
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          if (is_c) cdot_l = fma(coef * u[k][v], uj[k][v], cdot_l);
+          acc[k][v] = fma(coef, uj[k][v], acc[k][v]);
+        }
+    }
+    red[0] += (double)cdot_l;
+    if (lane_g == 0) red[0] += a.cdiag[i] * (double)nrm;
+
+    if (W != nullptr) {
+      const T dc = (T)dcoef;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int ch = lane_g + k * G;
+        if (ch < nch) {
+          T w[VEC];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) w[v] = fma(dc, u[k][v], acc[k][v]) + cj[k][v];
+          store_chunk<T>(W, rowoff + ch * VEC, w);
+        }
+      }
+    }
+  }
+  grid_reduce<3>(red, a.partials, a.counter, a.out);
+}
+
+// ---------------------------------------------------------------------------
+// g(Y) - g(X) without cancellation: every pair product difference is
+// <Y_a,Y_b> - <X_a,X_b> = <D_a, Y_b> + <X_a, D_b>, D = Y - X.
+// ---------------------------------------------------------------------------
+struct DiffIO {
+  const void* __restrict__ X;
+  const void* __restrict__ Y;
+  const double* __restrict__ rX;
+  double* __restrict__ rY;  // or null
+};
+
+template <class T, int FAM, int G, int K>
+__global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
+  using Tr = FamTraits<FAM>;
+  constexpr int VEC = V16<T>::N;
+  const T* __restrict__ X = static_cast<const T*>(io.X);
+  const T* __restrict__ Y = static_cast<const T*>(io.Y);
+  const T* __restrict__ cval = static_cast<const T*>(a.cval);
+  const int lane_g = threadIdx.x & (G - 1);
+  const unsigned gmask = group_mask<G>();
+  const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
+  const int nch = a.ld / VEC;
+
+  // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
+    T x[K][VEC], d[K][VEC];
+    const int64_t rowoff = i * (int64_t)a.ld;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int ch = lane_g + k * G;
+      T y[VEC];
+      if (ch < nch) {
+        load_chunk<T>(X, rowoff + ch * VEC, x[k]);
+        load_chunk<T>(Y, rowoff + ch * VEC, y);
+      } else {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) x[k][v] = y[v] = (T)0;
+      }
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) d[k][v] = y[v] - x[k][v];
+    }
+    // <D_i, Y_i + X_i> = <D_i, D_i + 2 X_i> = |Y_i|^2 - |X_i|^2
+    T own_l = (T)0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) own_l = fma(d[k][v], d[k][v] + (T)2 * x[k][v], own_l);
+    red[3] += (double)own_l;               // trace row change (lane parts)
+    red[0] += a.cdiag[i] * (double)own_l;  // diagonal of C
+    if (Tr::kDiag) {
+      const T dTi = group_sum<G>(own_l, gmask);
+      if (lane_g == 0) {
+        const double dt = (double)dTi, rx = io.rX[i];
+        red[1] += a.p[i] * dt;
+        red[2] += dt * (2.0 * rx + dt);
+        if (io.rY) io.rY[i] = rx + dt;
+      }
+    }
+    const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
+    T cd_l = (T)0;
+#pragma unroll 2
+    for (int e = e0; e < e1; ++e) {
+      int cd = 0;
+      if (Tr::kPairs) {
+        cd = a.code[e];
+        if (cd < 0 && cd != kNoCons) continue;  // mirrored pair entry: the owner row does it
+        if (!Tr::kCval && cd == kNoCons) continue;
+      }
+      const int64_t j = a.col[e];
+      T pd = (T)0;  // lane part of <D_i, Y_j> + <X_i, D_j>
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int ch = lane_g + k * G;
+        if (ch < nch) {
+          T xj[VEC], yj[VEC];
+          load_chunk_l2<T>(X, j * a.ld + ch * VEC, xj);
+          load_chunk_l2<T>(Y, j * a.ld + ch * VEC, yj);
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            pd = fma(d[k][v], yj[v], pd);
+            pd = fma(x[k][v], yj[v] - xj[v], pd);
+          }
+        }
+      }
+      if (Tr::kDiag || cd == kNoCons) {
+        cd_l = fma(cval[e], pd, cd_l);
+      } else {
+        // owned pair constraint l: dT_l = <Y_i,Y_j> - <X_i,X_j>
+        const T dTl = group_sum<G>(pd, gmask);
+        if (lane_g == 0) {
+          const double dt = (double)dTl, rx = io.rX[cd];
+          red[1] += a.p[cd] * dt;
+          red[2] += dt * (2.0 * rx + dt);
+          if (io.rY) io.rY[cd] = rx + dt;
+        }
+      }
+    }
+    red[0] += (double)cd_l;
+  }
+  grid_reduce<4>(red, a.partials, a.counter, a.out);
+}
+
+// ---------------------------------------------------------------------------
+// pre-passes: column sums (C_J part) and |U|_F^2 (trace row)
+// ---------------------------------------------------------------------------
+// Thread t of a block owns column t mod ld of every (256 / ld)-th row; the
+// per-thread sums are combined per column in a fixed order, so each block's
+// partial row and the last block's total are deterministic.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int64_t n, int ld,
+                                                   int mode, const T* __restrict__ Y,
+                                                   double* partials, unsigned* counter,
+                                                   double* colsum_out, double* colsum_out2,
+                                                   double* scal_out) {
+  // mode 0: s = colsum(U), scal = [|U|_F^2, |s|^2]
+  // mode 1: X = U, D = Y - X: s = colsum(D), s2 = colsum(Y + X),
+  //         scal = [sum <D_i, Y_i + X_i>, <s, s2>]
+  __shared__ double t1[kBlock], t2[kBlock];
+  __shared__ double sh[kColsumMax], sh2[kColsumMax];
+  __shared__ double shr[1][kBlock / 32];
+  __shared__ bool am_last;
+  const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
+  const int c = threadIdx.x % ld;
+  const int rsub = threadIdx.x / ld;
+  double acc = 0.0, acc2 = 0.0, nrm = 0.0;
+  if (rsub < rows_per_pass) {
+    for (int64_t i = (int64_t)blockIdx.x * rows_per_pass + rsub; i < n;
+         i += (int64_t)gridDim.x * rows_per_pass) {
+      const T xv = U[i * ld + c];
+      const double x = (double)xv;
+      if (mode == 0) {
+        acc += x;
+        nrm += x * x;
+      } else {
+        const T yv = Y[i * ld + c];
+        const double y = (double)yv;
+        const double dd = (double)(yv - xv);
+        acc += dd;
+        acc2 += y + x;
+        nrm += dd * (y + x);
+      }
+    }
+  }
+  t1[threadIdx.x] = acc;
+  t2[threadIdx.x] = acc2;
+  double red[1] = {nrm};
+  block_sum<1>(red, shr);  // contains __syncthreads
+  const int W = ld + 1;
+  for (int cc = threadIdx.x; cc < ld; cc += kBlock) {
+    double s = 0.0, s2 = 0.0;
+    for (int q = 0; q < rows_per_pass; ++q) {
+      s += t1[q * ld + cc];
+      s2 += t2[q * ld + cc];
+    }
+    partials[(size_t)blockIdx.x * (2 * W) + cc] = s;
+    partials[(size_t)blockIdx.x * (2 * W) + W + cc] = s2;
+  }
+  if (threadIdx.x == 0) partials[(size_t)blockIdx.x * (2 * W) + ld] = red[0];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int cc = threadIdx.x; cc <= ld; cc += kBlock) {
+    double s = 0.0, s2 = 0.0;
+    for (unsigned bb = 0; bb < gridDim.x; ++bb) {
+      s += __ldcg(&partials[(size_t)bb * (2 * W) + cc]);
+      if (cc < ld) s2 += __ldcg(&partials[(size_t)bb * (2 * W) + W + cc]);
+    }
+    if (cc < ld) {
+      sh[cc] = s;
+      sh2[cc] = s2;
+      colsum_out[cc] = s;
+      if (colsum_out2) colsum_out2[cc] = s2;
+    } else {
+      scal_out[0] = s;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q = 0.0;
+    for (int cc = 0; cc < ld; ++cc) q += (mode == 0 ? sh[cc] * sh[cc] : sh[cc] * sh2[cc]);
+    scal_out[1] = q;
+    *counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Frank-Wolfe denominator sum_l (A_l.YY^T - tau^2 A_l.yy^T)^2 over the
+// non-trace constraints, with A_l.YY^T = r_l + b_l (FP64, r = 1 gathers)
+// ---------------------------------------------------------------------------
+template <int FAM>
+__global__ void __launch_bounds__(kBlock) k_fw_denom(OpArgs a, const double* __restrict__ y,
+                                                     const double* __restrict__ resid,
+                                                     double tau2) {
+  using Tr = FamTraits<FAM>;
+  double red[2] = {0.0, 0.0};  // sum of squares, |y|^2
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const double yi = y[i];
+    red[1] += yi * yi;
+    if (Tr::kDiag) {
+      const double dl = resid[i] + a.b[i] - tau2 * yi * yi;
+      red[0] += dl * dl;
+    } else {
+      const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
+      for (int e = e0; e < e1; ++e) {
+        const int cd = a.code[e];
+        if (cd < 0) continue;  // mirrored or pure C entry
+        const double dl = resid[cd] + a.b[cd] - tau2 * yi * __ldcg(&y[a.col[e]]);
+        red[0] += dl * dl;
+      }
+    }
+  }
+  grid_reduce<2>(red, a.partials, a.counter, a.out);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+OpArgs make_args(Ctx* c, int ld, int slot) {
+  const Problem& P = c->P;
+  OpArgs a;
+  a.n = P.n;
+  a.ld = ld;
+  a.rowptr = P.rowptr;
+  a.col = P.col;
+  a.code = P.code;
+  a.cval = c->opt.precision == HALLAR_MIXED ? (const void*)P.cval32 : (const void*)P.cval;
+  a.cdiag = P.cdiag;
+  a.b = P.b;
+  a.p = nullptr;
+  a.C_J = P.C_J;
+  a.beta = 0.0;
+  a.has_trace = P.has_trace;
+  a.trace_row = P.m - 1;
+  a.partials = c->red.partials;
+  a.counter = c->red.counter;
+  a.out = c->d_scal + slot;
+  return a;
+}
+
+struct Shape {
+  int G, K;
+};
+Shape pick_shape(int ld, int vec) {
+  const int nch = ld / vec;
+  if (nch <= 32) {
+    int G = 2;
+    while (G < nch) G <<= 1;
+    return {G, 1};
+  }
+  const int K = (nch + 31) / 32;
+  return {32, K <= 2 ? 2 : 4};
+}
+
+// run `body` with the row-group shape template arguments G and K for `ld`
+#define HL_BY_SHAPE(T_, ld, ...)                                      \
+  do {                                                                 \
+    const Shape s__ = pick_shape((ld), V16<T_>::N);                    \
+    switch (s__.G * 10 + s__.K) {                                      \
+      case 21: { constexpr int G = 2, K = 1; __VA_ARGS__; } break;            \
+      case 41: { constexpr int G = 4, K = 1; __VA_ARGS__; } break;            \
+      case 81: { constexpr int G = 8, K = 1; __VA_ARGS__; } break;            \
+      case 161: { constexpr int G = 16, K = 1; __VA_ARGS__; } break;          \
+      case 321: { constexpr int G = 32, K = 1; __VA_ARGS__; } break;          \
+      case 322: { constexpr int G = 32, K = 2; __VA_ARGS__; } break;          \
+      case 324: { constexpr int G = 32, K = 4; __VA_ARGS__; } break;          \
+      default: fail(HALLAR_EINVAL, "unsupported factor width");        \
+    }                                                                  \
+  } while (0)
+
+// run `body` with T (factor type) and FAM (kernel family) of the handle
+#define HL_BY_FAM_TYPE(c, ...)                                                         \
+  do {                                                                                  \
+    const bool mixed__ = (c)->opt.precision == HALLAR_MIXED;                            \
+    switch ((c)->P.fam) {                                                               \
+      case FAM_DIAG:                                                                    \
+        if (mixed__) { using T = float; constexpr int FAM = FAM_DIAG; __VA_ARGS__; }           \
+        else { using T = double; constexpr int FAM = FAM_DIAG; __VA_ARGS__; }                  \
+        break;                                                                          \
+      case FAM_EDGE:                                                                    \
+        if (mixed__) { using T = float; constexpr int FAM = FAM_EDGE; __VA_ARGS__; }           \
+        else { using T = double; constexpr int FAM = FAM_EDGE; __VA_ARGS__; }                  \
+        break;                                                                          \
+      default:                                                                          \
+        if (mixed__) { using T = float; constexpr int FAM = FAM_EDGE_C; __VA_ARGS__; }         \
+        else { using T = double; constexpr int FAM = FAM_EDGE_C; __VA_ARGS__; }                \
+        break;                                                                          \
+    }                                                                                   \
+  } while (0)
+
+}  // namespace
+
+void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double beta,
+                 const double* colsum, GradOut out) {
+  (void)r;
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  OpArgs a = make_args(c, ld, S_GRAD);
+  a.p = p;
+  a.beta = beta;
+  GradIO io;
+  io.U = U;
+  io.colsum = (c->P.C_J != 0.0) ? colsum : nullptr;
+  io.pre = c->d_scal + S_PRE;
+  io.W = out.W;
+  io.resid = out.resid;
+  io.Tout = out.T ? out.T + 1 : nullptr;
+  HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
+    const int grid = grid_for(c, a.n, kBlock / G);
+    k_grad<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
+  }));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const double* p,
+                         const double* rX, double* rY) {
+  (void)r;
+  OpArgs a = make_args(c, ld, S_DIFF);
+  a.p = p;
+  DiffIO io{X, Y, rX, rY};
+  HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
+    const int grid = grid_for(c, a.n, kBlock / G);
+    k_value_change<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
+  }));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot) {
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
+  const int grid = grid_for(c, c->P.n, rows_per_pass * 8);
+  if (c->opt.precision == HALLAR_MIXED)
+    k_colsum<float><<<grid, kBlock, 0, c->stream>>>(
+        (const float*)U, c->P.n, ld, 0, nullptr, c->red.partials, c->red.counter, colsum_out,
+        nullptr, c->d_scal + slot);
+  else
+    k_colsum<double><<<grid, kBlock, 0, c->stream>>>(
+        (const double*)U, c->P.n, ld, 0, nullptr, c->red.partials, c->red.counter, colsum_out,
+        nullptr, c->d_scal + slot);
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD, double* sS) {
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
+  const int grid = grid_for(c, c->P.n, rows_per_pass * 8);
+  if (c->opt.precision == HALLAR_MIXED)
+    k_colsum<float><<<grid, kBlock, 0, c->stream>>>(
+        (const float*)X, c->P.n, ld, 1, (const float*)Y, c->red.partials, c->red.counter, sD,
+        sS, c->d_scal + S_DIFF + 4);
+  else
+    k_colsum<double><<<grid, kBlock, 0, c->stream>>>(
+        (const double*)X, c->P.n, ld, 1, (const double*)Y, c->red.partials, c->red.counter, sD,
+        sS, c->d_scal + S_DIFF + 4);
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_fw_denom(Ctx* c, const double* y, const double* resid, double tau2, int slot) {
+  OpArgs a = make_args(c, 1, slot);
+  const int grid = grid_for(c, c->P.n, kBlock);
+  switch (c->P.fam) {
+    case FAM_DIAG: k_fw_denom<FAM_DIAG><<<grid, kBlock, 0, c->stream>>>(a, y, resid, tau2); break;
+    case FAM_EDGE: k_fw_denom<FAM_EDGE><<<grid, kBlock, 0, c->stream>>>(a, y, resid, tau2); break;
+    default: k_fw_denom<FAM_EDGE_C><<<grid, kBlock, 0, c->stream>>>(a, y, resid, tau2); break;
+  }
+  HL_CHECK_LAUNCH(c);
+}
+
+}  // namespace hallar

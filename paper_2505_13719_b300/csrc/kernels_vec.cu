@@ -1,0 +1,416 @@
+// Streaming kernels of ADAP-FISTA / ADAP-AIPP (Appendix A), the Frank-Wolfe
+// rank update (eq. tilde Y) and the rank trim.  Every kernel is one pass over
+// n x ld factor arrays with 16-byte vector accesses, and folds the Frobenius
+// norms and inner products the host needs into the same pass (FP64
+// accumulation, deterministic grid reduction).  Padding columns are zero and
+// every update here is linear, so they stay zero.
+#include "device_common.cuh"
+#include "hallar_internal.cuh"
+
+namespace hallar {
+
+namespace {
+
+template <class T, int NS, class Op>
+__global__ void __launch_bounds__(kBlock) k_stream(int64_t nvec, Op op, double* partials,
+                                                   unsigned* counter, double* out) {
+  double red[NS > 0 ? NS : 1];
+#pragma unroll
+  for (int s = 0; s < (NS > 0 ? NS : 1); ++s) red[s] = 0.0;
+  for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < nvec;
+       v += (int64_t)gridDim.x * kBlock)
+    op(v, red);
+  if constexpr (NS > 0) grid_reduce<NS>(red, partials, counter, out);
+}
+
+template <class T, int NS, class Op>
+void run_stream(Ctx* c, int64_t nelem, const Op& op, int slot) {
+  constexpr int VEC = V16<T>::N;
+  const int64_t nvec = nelem / VEC;
+  const int grid = grid_for(c, nvec, kBlock * 4);
+  k_stream<T, NS, Op><<<grid, kBlock, 0, c->stream>>>(nvec, op, c->red.partials, c->red.counter,
+                                                      c->d_scal + (slot >= 0 ? slot : 0));
+  HL_CHECK_LAUNCH(c);
+}
+
+#define HL_LOAD(ptr, v, arr) load_chunk<T>((ptr), (v) * VEC, arr)
+
+// xt = (A y + a x) / (A + a)      (ADAP-FISTA step 2)
+template <class T>
+struct OpXt {
+  T* xt; const T* y; const T* x; double wy, wx;
+  __device__ void operator()(int64_t v, double*) const {
+    constexpr int VEC = V16<T>::N;
+    T a[VEC], b[VEC], o[VEC];
+    HL_LOAD(y, v, a);
+    HL_LOAD(x, v, b);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) o[k] = (T)(wy * (double)a[k] + wx * (double)b[k]);
+    store_chunk<T>(xt, v * VEC, o);
+  }
+};
+
+// x <- (mu a y + tk x - a s) / tk_new, s = (L - mu)(xt - y)   (step 3)
+template <class T>
+struct OpX {
+  T* x; const T* y; const T* xt; double cy, cx, cxt;
+  __device__ void operator()(int64_t v, double*) const {
+    constexpr int VEC = V16<T>::N;
+    T a[VEC], b[VEC], t[VEC], o[VEC];
+    HL_LOAD(y, v, a);
+    HL_LOAD(x, v, b);
+    HL_LOAD(xt, v, t);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k)
+      o[k] = (T)(cy * (double)a[k] + cx * (double)b[k] + cxt * (double)t[k]);
+    store_chunk<T>(x, v * VEC, o);
+  }
+};
+
+// z = xt - grad psi_s(xt) / L with grad psi_s = 2 lam W + xt - center;
+// red[0] = |z|^2 (the ball projection is the scaling min(1, tau/|z|))
+template <class T>
+struct OpZ {
+  T* z; const T* xt; const T* W; const T* ctr; double c2lam, invL;
+  __device__ void operator()(int64_t v, double* red) const {
+    constexpr int VEC = V16<T>::N;
+    T a[VEC], w[VEC], cc[VEC], o[VEC];
+    HL_LOAD(xt, v, a);
+    HL_LOAD(W, v, w);
+    HL_LOAD(ctr, v, cc);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const double g = c2lam * (double)w[k] + ((double)a[k] - (double)cc[k]);
+      o[k] = (T)((double)a[k] - invL * g);
+      red[0] += (double)o[k] * (double)o[k];
+    }
+    store_chunk<T>(z, v * VEC, o);
+  }
+};
+
+// y = c z with c = min(1, tau/|z|) (|z|^2 read from the device); with
+// d = y - xt and g = grad psi_s(xt) = 2 lam W + xt - center:
+// red = [|d|^2, <g, d>, <d, (y + xt)/2 - center>, |y - center|^2]
+template <class T>
+struct OpY {
+  T* y; const T* z; const T* xt; const T* ctr; const T* W; const double* z2; double tau, c2lam;
+  __device__ void operator()(int64_t v, double* red) const {
+    constexpr int VEC = V16<T>::N;
+    const double zn = sqrt(*z2);
+    const double cs = zn > tau ? tau / zn : 1.0;
+    T zz[VEC], a[VEC], cc[VEC], w[VEC], o[VEC];
+    HL_LOAD(z, v, zz);
+    HL_LOAD(xt, v, a);
+    HL_LOAD(ctr, v, cc);
+    HL_LOAD(W, v, w);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      o[k] = (T)(cs * (double)zz[k]);
+      const double yk = (double)o[k], xk = (double)a[k], ck = (double)cc[k];
+      const double d = yk - xk;
+      const double g = c2lam * (double)w[k] + (xk - ck);
+      red[0] += d * d;
+      red[1] += g * d;
+      red[2] += d * (0.5 * (yk + xk) - ck);
+      red[3] += (yk - ck) * (yk - ck);
+    }
+    store_chunk<T>(y, v * VEC, o);
+  }
+};
+
+// ADAP-AIPP step 2-3 pieces at the FISTA output y (z its unprojected step):
+// V = 2 lam W(y) + (y - center) + L (z - y), D = y - center:
+// red = [<V, D>, |D|^2, |V - D|^2]   (R_j = (V - D) / lam, eq. Rj def)
+template <class T>
+struct OpAipp {
+  const T* Wy; const T* z; const T* y; const T* ctr; double c2lam, L;
+  __device__ void operator()(int64_t v, double* red) const {
+    constexpr int VEC = V16<T>::N;
+    T w[VEC], zz[VEC], yy[VEC], cc[VEC];
+    HL_LOAD(Wy, v, w);
+    HL_LOAD(z, v, zz);
+    HL_LOAD(y, v, yy);
+    HL_LOAD(ctr, v, cc);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      const double D = (double)yy[k] - (double)cc[k];
+      const double VmD = c2lam * (double)w[k] + L * ((double)zz[k] - (double)yy[k]);
+      const double V = VmD + D;
+      red[0] += V * D;
+      red[1] += D * D;
+      red[2] += VmD * VmD;
+    }
+  }
+};
+
+template <class T>
+struct OpScale {
+  T* u; double s;
+  __device__ void operator()(int64_t v, double*) const {
+    constexpr int VEC = V16<T>::N;
+    T a[VEC];
+    HL_LOAD(u, v, a);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) a[k] = (T)(s * (double)a[k]);
+    store_chunk<T>(u, v * VEC, a);
+  }
+};
+
+template <class T>
+struct OpNorm2 {
+  const T* u;
+  __device__ void operator()(int64_t v, double* red) const {
+    constexpr int VEC = V16<T>::N;
+    T a[VEC];
+    HL_LOAD(u, v, a);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) red[0] += (double)a[k] * (double)a[k];
+  }
+};
+
+template <class T>
+struct OpDot {
+  const T* a; const T* b;
+  __device__ void operator()(int64_t v, double* red) const {
+    constexpr int VEC = V16<T>::N;
+    T x[VEC], y[VEC];
+    HL_LOAD(a, v, x);
+    HL_LOAD(b, v, y);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) red[0] += (double)x[k] * (double)y[k];
+  }
+};
+
+// padded, scaled row copy: dst[i, 0:r_copy] = s * src[i, 0:r_copy], rest 0
+template <class T>
+__global__ void k_pad_copy(const T* __restrict__ src, int ld_src, T* __restrict__ dst, int ld_dst,
+                           int r_copy, int64_t n, double s) {
+  const int64_t total = n * ld_dst;
+  for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kBlock) {
+    const int64_t i = e / ld_dst;
+    const int c = (int)(e - i * ld_dst);
+    dst[e] = c < r_copy ? (T)(s * (double)src[i * ld_src + c]) : (T)0;
+  }
+}
+
+// Frank-Wolfe factor (eq. tilde Y): Ynew[i, :r] = sY Y[i, :r],
+// Ynew[i, r] = sy y_i when appending, zero padding
+template <class T>
+__global__ void k_fw_append(const T* __restrict__ Y, int ld, int r, const double* __restrict__ y,
+                            double sY, double sy, T* __restrict__ Yn, int ld_new, int append,
+                            int64_t n) {
+  const int64_t total = n * ld_new;
+  for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kBlock) {
+    const int64_t i = e / ld_new;
+    const int c = (int)(e - i * ld_new);
+    double val = 0.0;
+    if (c < r) val = sY * (double)Y[i * ld + c];
+    else if (append && c == r) val = sy * y[i];
+    Yn[e] = (T)val;
+  }
+}
+
+// m-length FP64 vectors: op 0: a = b + s c; op 1: red = <b, c>; op 2: red = |b|^2
+struct OpDvec {
+  int op; double* a; const double* b; const double* cc; double s;
+  __device__ void operator()(int64_t i, double* red) const {
+    if (op == 0) a[i] = b[i] + s * cc[i];
+    else if (op == 1) red[0] += b[i] * cc[i];
+    else red[0] += b[i] * b[i];
+  }
+};
+
+__global__ void __launch_bounds__(kBlock) k_dvec(int64_t len, OpDvec op, double* partials,
+                                                 unsigned* counter, double* out) {
+  double red[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * kBlock)
+    op(i, red);
+  grid_reduce<1>(red, partials, counter, out);
+}
+
+// Gram U^T U (rank trim): block b accumulates rows b*8.., stepping by the
+// grid, into its own r x r partial; a second kernel sums the partials in
+// block order.
+constexpr int kGramAcc = 32;  // r*r <= 32 * 256, i.e. r <= 90
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_gram_partial(const T* __restrict__ U, int ld, int r,
+                                                         int64_t n, double* __restrict__ part) {
+  extern __shared__ double rowbuf[];  // [8][ld]
+  const int npair = r * r;
+  double acc[kGramAcc];
+#pragma unroll
+  for (int q = 0; q < kGramAcc; ++q) acc[q] = 0.0;
+  for (int64_t i0 = (int64_t)blockIdx.x * 8; i0 < n; i0 += (int64_t)gridDim.x * 8) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < 8 * ld; e += kBlock) {
+      const int64_t i = i0 + e / ld;
+      rowbuf[e] = i < n ? (double)U[i * ld + (e % ld)] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kGramAcc; ++q) {
+      const int pr = threadIdx.x + q * kBlock;
+      if (pr < npair) {
+        const int a = pr / r, bcol = pr % r;
+        double s = 0.0;
+        for (int rr = 0; rr < 8; ++rr) s += rowbuf[rr * ld + a] * rowbuf[rr * ld + bcol];
+        acc[q] += s;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kGramAcc; ++q) {
+    const int pr = threadIdx.x + q * kBlock;
+    if (pr < npair) part[(size_t)blockIdx.x * npair + pr] = acc[q];
+  }
+}
+
+__global__ void k_sum_blocks(const double* __restrict__ part, int nblocks, int width,
+                             double* __restrict__ out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < width; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += part[(size_t)b * width + j];
+    out[j] = s;
+  }
+}
+
+// out[i, :k] = U[i, :r] Q (Q row-major r x k, FP64), zero padding to ld_out
+template <class T>
+__global__ void k_right_mult(const T* __restrict__ U, int ld, int r, const double* __restrict__ Q,
+                             int k, T* __restrict__ out, int ld_out, int64_t n) {
+  const int64_t total = n * ld_out;
+  for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kBlock) {
+    const int64_t i = e / ld_out;
+    const int c = (int)(e - i * ld_out);
+    double s = 0.0;
+    if (c < k)
+      for (int a = 0; a < r; ++a) s += (double)U[i * ld + a] * __ldg(&Q[a * k + c]);
+    out[e] = (T)s;
+  }
+}
+
+// run the statements with T the factor element type of the handle
+#define HL_BY_TYPE(c, ...)                                    \
+  do {                                                        \
+    if ((c)->opt.precision == HALLAR_MIXED) {                 \
+      using T = float;                                        \
+      __VA_ARGS__;                                            \
+    } else {                                                  \
+      using T = double;                                       \
+      __VA_ARGS__;                                            \
+    }                                                         \
+  } while (0)
+
+}  // namespace
+
+void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, double a, int ld) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  const double wy = A / (A + a), wx = a / (A + a);
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXt<T>{(T*)xt, (const T*)y, (const T*)x, wy, wx}, -1));
+}
+
+void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, double a,
+                    double tk, double tk_new, double L, int ld) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  // x_new = [mu a y + tk x - a (L - mu)(xt - y)] / tk_new
+  const double cy = (mu * a + a * (L - mu)) / tk_new;
+  const double cx = tk / tk_new;
+  const double cxt = -a * (L - mu) / tk_new;
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpX<T>{(T*)x, (const T*)y, (const T*)xt, cy, cx, cxt}, -1));
+}
+
+void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,
+                    double lam, double L, int ld) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  const double c2lam = 2.0 * lam, invL = 1.0 / L;
+  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpZ<T>{(T*)z, (const T*)xt, (const T*)W, (const T*)center,
+                                               c2lam, invL}, S_SCALE));
+}
+
+void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* center,
+                    const void* W, double lam, double tau, int ld) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  const double* z2 = c->d_scal + S_SCALE;
+  const double c2lam = 2.0 * lam;
+  HL_BY_TYPE(c, run_stream<T, 4>(c, ne, OpY<T>{(T*)y, (const T*)z, (const T*)xt, (const T*)center,
+                                               (const T*)W, z2, tau, c2lam}, S_VEC));
+}
+
+void launch_aipp_check(Ctx* c, const void* Wy, const void* z, const void* y, const void* center,
+                       double lam, double L, int ld) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  const double c2lam = 2.0 * lam;
+  HL_BY_TYPE(c, run_stream<T, 3>(c, ne, OpAipp<T>{(const T*)Wy, (const T*)z, (const T*)y,
+                                                  (const T*)center, c2lam, L}, S_VEC2));
+}
+
+void launch_scale(Ctx* c, void* U, int ld, double s) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpScale<T>{(T*)U, s}, -1));
+}
+
+void launch_norm2(Ctx* c, const void* U, int ld, int slot) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpNorm2<T>{(const T*)U}, slot));
+}
+
+void launch_dot(Ctx* c, const void* W, const void* U, int ld, int slot) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpDot<T>{(const T*)W, (const T*)U}, slot));
+}
+
+void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst, int r_copy,
+                     double scale_src) {
+  const int64_t total = c->P.n * (int64_t)ld_dst;
+  const int grid = grid_for(c, total, kBlock * 4);
+  HL_BY_TYPE(c, k_pad_copy<T><<<grid, kBlock, 0, c->stream>>>((const T*)src, ld_src, (T*)dst,
+                                                             ld_dst, r_copy, c->P.n, scale_src));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_fw_append(Ctx* c, const void* Y, int ld, int r, const double* y, double sY, double sy,
+                      void* Ynew, int ld_new, int append) {
+  const int64_t total = c->P.n * (int64_t)ld_new;
+  const int grid = grid_for(c, total, kBlock * 4);
+  HL_BY_TYPE(c, k_fw_append<T><<<grid, kBlock, 0, c->stream>>>((const T*)Y, ld, r, y, sY, sy,
+                                                              (T*)Ynew, ld_new, append, c->P.n));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_dvec(Ctx* c, int op, int64_t len, double* a, const double* b, const double* cc,
+                 double s, int slot) {
+  const int grid = grid_for(c, len, kBlock * 4);
+  k_dvec<<<grid, kBlock, 0, c->stream>>>(len, OpDvec{op, a, b, cc, s}, c->red.partials,
+                                         c->red.counter,
+                                         c->d_scal + (slot >= 0 ? slot : S_VEC2 + 7));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_gram(Ctx* c, const void* U, int ld, int r, double* G) {
+  if (r * r > kGramAcc * kBlock) fail(HALLAR_EINVAL, "rank trim supports ranks up to 90");
+  int grid = grid_for(c, c->P.n, 8 * 8);
+  if (grid > 512) grid = 512;
+  double* part = (double*)ensure_buffer(c, &c->gram_part, &c->gram_part_bytes,
+                                        (size_t)grid * r * r * sizeof(double));
+  const size_t smem = (size_t)8 * ld * sizeof(double);
+  HL_BY_TYPE(c, k_gram_partial<T><<<grid, kBlock, smem, c->stream>>>((const T*)U, ld, r, c->P.n,
+                                                                     part));
+  HL_CHECK_LAUNCH(c);
+  k_sum_blocks<<<(r * r + 127) / 128, 128, 0, c->stream>>>(part, grid, r * r, G);
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_right_mult(Ctx* c, const void* U, int ld, int r, const double* Q, int k, void* out,
+                       int ld_out) {
+  const int64_t total = c->P.n * (int64_t)ld_out;
+  const int grid = grid_for(c, total, kBlock * 4);
+  HL_BY_TYPE(c, k_right_mult<T><<<grid, kBlock, 0, c->stream>>>((const T*)U, ld, r, Q, k, (T*)out,
+                                                               ld_out, c->P.n));
+  HL_CHECK_LAUNCH(c);
+}
+
+}  // namespace hallar

@@ -1,0 +1,503 @@
+// Minimum eigenpair of G = C + A*(p') (Alg. 1 step 7, eq. Grad X Space) by
+// Lanczos with full reorthogonalisation, in FP64 for both precision forms.
+//
+// The basis Q is stored row-major, n x kcap (row i holds q_0[i] .. q_k[i]),
+// so each pass of an iteration streams Q once with coalesced row reads, one
+// warp per row:
+//   pass 1  w = G q_k (SpMV over the merged CSR) and h = Q^T w
+//   pass 2  w <- w - Q h and h2 = Q^T w          (the second classical
+//   pass 3  w <- w - Q h2, |w|^2 and sum(w)       Gram-Schmidt sweep)
+// alpha_k = h_k + h2_k, beta_k = |w|; the host solves the k x k tridiagonal
+// (Sturm bisection + inverse iteration) and tests the Ritz residual.
+#include <cmath>
+#include <vector>
+
+#include "device_common.cuh"
+#include "hallar_internal.cuh"
+
+namespace hallar {
+
+namespace {
+
+constexpr int kLanMaxCols = 512;  // 16 accumulators per lane
+
+struct LanArgs {
+  int64_t n;
+  const int* __restrict__ rowptr;
+  const int* __restrict__ col;
+  const int* __restrict__ code;
+  const double* __restrict__ cval;
+  const double* __restrict__ cdiag;
+  double C_J;
+  int fam;
+  int has_trace;
+  int64_t trace_row;
+  const double* __restrict__ ps;  // p'
+};
+
+// per-warp partial column sums -> per-block partial rows (fixed order)
+template <int NACC>
+__device__ inline void write_block_partial(double (&acc)[NACC], int ncols,
+                                           double* __restrict__ part) {
+  __shared__ double sh[kBlock / 32][kLanMaxCols];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NACC; ++t) {
+    const int j = lane + 32 * t;
+    if (j < ncols) sh[warp][j] = acc[t];
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ncols; j += kBlock) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += sh[w][j];
+    part[(size_t)blockIdx.x * ncols + j] = s;
+  }
+}
+
+__device__ inline double gv_row(const LanArgs& a, int64_t i, const double* __restrict__ v,
+                                 double vscale, double vsum, double vi, int lane, int stride) {
+  // lanes lane, lane + stride, ... of the row's entries; caller reduces
+  double s = 0.0;
+  for (int e = a.rowptr[i] + lane; e < a.rowptr[i + 1]; e += stride) {
+    const double vj = __ldcg(&v[a.col[e]]) * vscale;
+    double coef;
+    if (a.fam == FAM_DIAG) {
+      coef = a.cval[e];
+    } else {
+      const int cd = a.code[e];
+      coef = cd == kNoCons ? a.cval[e] : 0.5 * a.ps[cd >= 0 ? cd : -cd - 1];
+    }
+    s = fma(coef, vj, s);
+  }
+  if (lane == 0) {
+    double dc = a.cdiag[i];
+    if (a.fam == FAM_DIAG) dc += a.ps[i];
+    else if (a.has_trace) dc += a.ps[a.trace_row];
+    s = fma(dc, vi, s) + a.C_J * vsum;
+  }
+  return s;
+}
+
+// pass 1: w = G v, v = vin * vscale (stored as column k of Q); h = Q[:, :k+1]^T w
+template <int NACC>
+__global__ void __launch_bounds__(kBlock) k_lan_spmv(LanArgs a, const double* __restrict__ vin,
+                                                     double vscale, double vsum,
+                                                     double* __restrict__ Q, int kcap, int k,
+                                                     double* __restrict__ w,
+                                                     double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
+  const int ncols = k + 1;
+  double acc[NACC];
+#pragma unroll
+  for (int t = 0; t < NACC; ++t) acc[t] = 0.0;
+  for (int64_t i = warp; i < a.n; i += nwarps) {
+    const double vi = vin[i] * vscale;
+    double s = gv_row(a, i, vin, vscale, vsum, vi, lane, 32);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double wi = s;
+    double* __restrict__ qrow = Q + i * (int64_t)kcap;
+#pragma unroll
+    for (int t = 0; t < NACC; ++t) {
+      const int j = lane + 32 * t;
+      if (j < k) acc[t] = fma(qrow[j], wi, acc[t]);
+      else if (j == k) acc[t] = fma(vi, wi, acc[t]);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      w[i] = wi;
+      qrow[k] = vi;
+    }
+  }
+  write_block_partial<NACC>(acc, ncols, part);
+}
+
+// pass 2: w <- w - Q h and h2 = Q^T w   (ncols = k + 1)
+template <int NACC>
+__global__ void __launch_bounds__(kBlock) k_lan_orth(int64_t n, const double* __restrict__ Q,
+                                                     int kcap, int ncols,
+                                                     const double* __restrict__ h,
+                                                     double* __restrict__ w,
+                                                     double* __restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
+  double hv[NACC], acc[NACC];
+#pragma unroll
+  for (int t = 0; t < NACC; ++t) {
+    const int j = lane + 32 * t;
+    hv[t] = j < ncols ? h[j] : 0.0;
+    acc[t] = 0.0;
+  }
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const double* __restrict__ qrow = Q + i * (int64_t)kcap;
+    double q[NACC];
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < NACC; ++t) {
+      const int j = lane + 32 * t;
+      q[t] = j < ncols ? qrow[j] : 0.0;
+      s = fma(q[t], hv[t], s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double wi = w[i] - s;
+#pragma unroll
+    for (int t = 0; t < NACC; ++t) acc[t] = fma(q[t], wi, acc[t]);
+    __syncwarp();
+    if (lane == 0) w[i] = wi;
+  }
+  write_block_partial<NACC>(acc, ncols, part);
+}
+
+// pass 3: w <- w - Q h2; reductions |w|^2 and sum(w) (ncols = 0: only the sums)
+template <int NACC>
+__global__ void __launch_bounds__(kBlock) k_lan_final(int64_t n, const double* __restrict__ Q,
+                                                      int kcap, int ncols,
+                                                      const double* __restrict__ h,
+                                                      double* __restrict__ w, double* partials,
+                                                      unsigned* counter, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
+  double hv[NACC];
+#pragma unroll
+  for (int t = 0; t < NACC; ++t) {
+    const int j = lane + 32 * t;
+    hv[t] = j < ncols ? h[j] : 0.0;
+  }
+  double red[2] = {0.0, 0.0};
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const double* __restrict__ qrow = Q + i * (int64_t)kcap;
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < NACC; ++t) {
+      const int j = lane + 32 * t;
+      if (j < ncols) s = fma(qrow[j], hv[t], s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double wi = w[i] - s;
+    __syncwarp();
+    if (lane == 0) {
+      if (ncols > 0) w[i] = wi;
+      red[0] += wi * wi;
+      red[1] += wi;
+    }
+  }
+  grid_reduce<2>(red, partials, counter, out);
+}
+
+// v = Q s (Ritz vector), |v|^2 into out[0]
+template <int NACC>
+__global__ void __launch_bounds__(kBlock) k_lan_combine(int64_t n, const double* __restrict__ Q,
+                                                        int kcap, int ncols,
+                                                        const double* __restrict__ s,
+                                                        double* __restrict__ v, double* partials,
+                                                        unsigned* counter, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
+  double sv[NACC];
+#pragma unroll
+  for (int t = 0; t < NACC; ++t) {
+    const int j = lane + 32 * t;
+    sv[t] = j < ncols ? s[j] : 0.0;
+  }
+  double red[1] = {0.0};
+  for (int64_t i = warp; i < n; i += nwarps) {
+    const double* __restrict__ qrow = Q + i * (int64_t)kcap;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < NACC; ++t) {
+      const int j = lane + 32 * t;
+      if (j < ncols) acc = fma(qrow[j], sv[t], acc);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      v[i] = acc;
+      red[0] += acc * acc;
+    }
+  }
+  grid_reduce<1>(red, partials, counter, out);
+}
+
+// sum the per-block partial rows: out[j] = sum_b part[b][j], one warp per column
+__global__ void k_sum_cols(const double* __restrict__ part, int nblocks, int ncols,
+                           double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (j >= ncols) return;
+  double s = 0.0;
+  for (int b = lane; b < nblocks; b += 32) s += part[(size_t)b * ncols + j];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[j] = s;
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014): element k (1-based) of stream
+// `seed` is the 64-bit finaliser of seed + k * 0x9E3779B97F4A7C15; the top
+// 53 bits give u in [0, 1) and the value used is 2u - 1.
+__global__ void k_splitmix(uint64_t seed, int64_t n, double* __restrict__ out, double mix_scale,
+                           const double* __restrict__ base) {
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    const double r = 2.0 * u - 1.0;
+    out[i] = base ? base[i] + mix_scale * r : r;
+  }
+}
+
+__global__ void k_dscale(int64_t n, double* __restrict__ v, double s) {
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock)
+    v[i] *= s;
+}
+
+// |G v - lambda v|^2 (one thread per row)
+__global__ void __launch_bounds__(kBlock) k_lan_resid(LanArgs a, const double* __restrict__ v,
+                                                      double vsum, double lambda,
+                                                      double* partials, unsigned* counter,
+                                                      double* out) {
+  double red[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const double gv = gv_row(a, i, v, 1.0, vsum, v[i], 0, 1);
+    const double d = gv - lambda * v[i];
+    red[0] += d * d;
+  }
+  grid_reduce<1>(red, partials, counter, out);
+}
+
+// ---------------------------------------------------------------------------
+// host: smallest eigenpair of a symmetric tridiagonal matrix
+// ---------------------------------------------------------------------------
+// Sturm count: number of eigenvalues below x of T = tridiag(beta, alpha, beta),
+// from the signs of the pivots of T - x I = L D L^T.
+int sturm_count(const std::vector<double>& al, const std::vector<double>& be, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+    d = (al[i] - x) - (i > 0 ? b2 / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// smallest eigenvalue by bisection on the Sturm count, eigenvector by
+// inverse iteration with a shift just below it
+double tridiag_min_eig(const std::vector<double>& al, const std::vector<double>& be, int k,
+                       std::vector<double>& s) {
+  double lo = al[0], hi = al[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(be[i]) : 0.0);
+    lo = std::fmin(lo, al[i] - r);
+    hi = std::fmax(hi, al[i] + r);
+  }
+  const double scale = std::fmax(std::fabs(lo), std::fabs(hi));
+  for (int it = 0; it < 200 && hi - lo > 4e-16 * scale; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(al, be, k, mid) >= 1) hi = mid;
+    else lo = mid;
+  }
+  const double lam = 0.5 * (lo + hi);
+  const double sigma = lam - 1e-13 * std::fmax(1.0, scale);
+  s.assign(k, 1.0);
+  std::vector<double> dd(k), x(k);
+  for (int rep = 0; rep < 3; ++rep) {
+    // (T - sigma I) x = s by Gaussian elimination without pivoting: T - sigma I
+    // is positive definite up to rounding since sigma is below lambda_min
+    double piv = al[0] - sigma;
+    if (std::fabs(piv) < 1e-300) piv = 1e-300;
+    dd[0] = piv;
+    x[0] = s[0];
+    for (int i = 1; i < k; ++i) {
+      const double l = be[i - 1] / dd[i - 1];
+      double p = (al[i] - sigma) - l * be[i - 1];
+      if (std::fabs(p) < 1e-300) p = 1e-300;
+      dd[i] = p;
+      x[i] = s[i] - l * x[i - 1];
+    }
+    x[k - 1] /= dd[k - 1];
+    for (int i = k - 2; i >= 0; --i) x[i] = (x[i] - be[i] * x[i + 1]) / dd[i];
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += x[i] * x[i];
+    nrm = std::sqrt(nrm);
+    for (int i = 0; i < k; ++i) s[i] = x[i] / nrm;
+  }
+  return lam;
+}
+
+// run `body` with NACC = accumulators per lane for `ncols` basis columns
+#define HL_BY_NACC(ncols, ...)                        \
+  do {                                                \
+    if ((ncols) <= 32) {                              \
+      constexpr int NACC = 1;                         \
+      __VA_ARGS__;                                    \
+    } else if ((ncols) <= 64) {                       \
+      constexpr int NACC = 2;                         \
+      __VA_ARGS__;                                    \
+    } else if ((ncols) <= 128) {                      \
+      constexpr int NACC = 4;                         \
+      __VA_ARGS__;                                    \
+    } else if ((ncols) <= 256) {                      \
+      constexpr int NACC = 8;                         \
+      __VA_ARGS__;                                    \
+    } else {                                          \
+      constexpr int NACC = 16;                        \
+      __VA_ARGS__;                                    \
+    }                                                 \
+  } while (0)
+
+}  // namespace
+
+void launch_splitmix(Ctx* c, uint64_t seed, double* out, double mix_scale, const double* base) {
+  k_splitmix<<<grid_for(c, c->P.n, kBlock * 4), kBlock, 0, c->stream>>>(seed, c->P.n, out,
+                                                                        mix_scale, base);
+  HL_CHECK_LAUNCH(c);
+}
+
+LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, double tol, int kmax,
+                           int max_restarts, double* v_out) {
+  const int64_t n = c->P.n;
+  if (kmax < 2) kmax = 2;
+  if (kmax > kLanMaxCols) kmax = kLanMaxCols;
+  if (kmax > n) kmax = (int)n;
+  const int kcap = (kmax + 3) / 4 * 4;
+  int grid = grid_for(c, n, (kBlock / 32) * 4);
+  if (grid > 1184) grid = 1184;
+  // workspace kept by the handle between calls
+  double* Q = (double*)ensure_buffer(c, &c->lan_Q, &c->lan_Q_bytes,
+                                     (size_t)n * kcap * sizeof(double));
+  double* w = (double*)ensure_buffer(c, &c->lan_w, &c->lan_w_bytes, 2 * (size_t)n * sizeof(double));
+  double* vin = w + n;
+  double* part = (double*)ensure_buffer(c, &c->lan_part, &c->lan_part_bytes,
+                                        (size_t)grid * kcap * sizeof(double));
+  double* hbuf = (double*)ensure_buffer(c, &c->lan_h, &c->lan_h_bytes,
+                                        3 * (size_t)kcap * sizeof(double));
+  double* h = hbuf;
+  double* h2 = hbuf + kcap;
+  double* sdev = hbuf + 2 * kcap;
+  LanArgs a;
+  a.n = n;
+  a.rowptr = c->P.rowptr;
+  a.col = c->P.col;
+  a.code = c->P.code;
+  a.cval = c->P.cval;
+  a.cdiag = c->P.cdiag;
+  a.C_J = c->P.C_J;
+  a.fam = c->P.fam;
+  a.has_trace = c->P.has_trace;
+  a.trace_row = c->P.m - 1;
+  a.ps = pshift;
+
+  // |v|^2 and sum(v) of a vector: pass 3 with no basis columns
+  auto norm_and_sum = [&](double* vec, double& nrm2, double& sum) {
+    k_lan_final<1><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, 0, h, vec, c->red.partials,
+                                                   c->red.counter, c->d_scal + S_LAN + 4);
+    HL_CHECK_LAUNCH(c);
+    fetch_scalars(c, S_LAN + 4, 2);
+    nrm2 = c->h_scal[S_LAN + 4];
+    sum = c->h_scal[S_LAN + 5];
+  };
+
+  HL_CUDA(cudaMemcpyAsync(vin, v0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  LanczosOut res{0.0, INFINITY, 0, false};
+  std::vector<double> al, be, s;
+  int total = 0;
+  for (int restart = 0; restart <= max_restarts; ++restart) {
+    double nv2, vs;
+    norm_and_sum(vin, nv2, vs);
+    if (!(nv2 > 0.0) || !std::isfinite(nv2)) {
+      // degenerate start vector: use the SplitMix64 vector of the seed
+      launch_splitmix(c, c->opt.seed + 1, vin, 0.0, nullptr);
+      norm_and_sum(vin, nv2, vs);
+    }
+    double vscale = 1.0 / std::sqrt(nv2);
+    double vsum = vs * vscale;
+    al.clear();
+    be.clear();
+    double* cur_in = vin;
+    double* cur_w = w;
+    bool done = false;
+    int kk = 0;
+    for (int k = 0; k < kmax; ++k) {
+      const int ncols = k + 1;
+      HL_BY_NACC(ncols, k_lan_spmv<NACC><<<grid, kBlock, 0, c->stream>>>(
+                            a, cur_in, vscale, vsum, Q, kcap, k, cur_w, part));
+      HL_CHECK_LAUNCH(c);
+      k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h);
+      HL_CHECK_LAUNCH(c);
+      HL_BY_NACC(ncols, k_lan_orth<NACC><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, ncols, h,
+                                                                          cur_w, part));
+      HL_CHECK_LAUNCH(c);
+      k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h2);
+      HL_CHECK_LAUNCH(c);
+      HL_BY_NACC(ncols, k_lan_final<NACC><<<grid, kBlock, 0, c->stream>>>(
+                            n, Q, kcap, ncols, h2, cur_w, c->red.partials, c->red.counter,
+                            c->d_scal + S_LAN));
+      HL_CHECK_LAUNCH(c);
+      HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 2, h + k, sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+      HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 3, h2 + k, sizeof(double),
+                              cudaMemcpyDeviceToHost, c->stream));
+      fetch_scalars(c, S_LAN, 2);
+      ++total;
+      const double alpha = c->h_scal[S_LAN + 2] + c->h_scal[S_LAN + 3];
+      const double bnorm = std::sqrt(c->h_scal[S_LAN]);
+      if (!std::isfinite(alpha) || !std::isfinite(bnorm))
+        fail(HALLAR_ENUMERIC, "Lanczos: non-finite value");
+      al.push_back(alpha);
+      be.push_back(bnorm);
+      kk = k + 1;
+      res.lambda = tridiag_min_eig(al, be, kk, s);
+      res.resid = std::fabs(bnorm * s[kk - 1]);
+      if (res.resid <= tol || bnorm <= 1e-300 || kk == n) {
+        done = true;
+        break;
+      }
+      // next basis vector w / |w|, scaled on the fly by the next pass 1
+      vscale = 1.0 / bnorm;
+      vsum = c->h_scal[S_LAN + 1] * vscale;
+      std::swap(cur_in, cur_w);
+    }
+    // Ritz vector v = Q s, normalised
+    HL_CUDA(cudaMemcpyAsync(sdev, s.data(), kk * sizeof(double), cudaMemcpyHostToDevice,
+                            c->stream));
+    HL_BY_NACC(kk, k_lan_combine<NACC><<<grid, kBlock, 0, c->stream>>>(
+                       n, Q, kcap, kk, sdev, v_out, c->red.partials, c->red.counter,
+                       c->d_scal + S_LAN));
+    HL_CHECK_LAUNCH(c);
+    fetch_scalars(c, S_LAN, 1);
+    k_dscale<<<grid_for(c, n, kBlock * 4), kBlock, 0, c->stream>>>(
+        n, v_out, 1.0 / std::sqrt(c->h_scal[S_LAN]));
+    HL_CHECK_LAUNCH(c);
+    // true residual |G v - lambda v| of the Ritz pair
+    double vn2, vsv;
+    norm_and_sum(v_out, vn2, vsv);
+    k_lan_resid<<<grid_for(c, n, kBlock * 4), kBlock, 0, c->stream>>>(
+        a, v_out, vsv, res.lambda, c->red.partials, c->red.counter, c->d_scal + S_LAN);
+    HL_CHECK_LAUNCH(c);
+    fetch_scalars(c, S_LAN, 1);
+    res.resid = std::sqrt(c->h_scal[S_LAN]);
+    res.iters = total;
+    if (done && (res.resid <= 1.5 * tol || kk == n)) {
+      res.converged = res.resid <= 1.5 * tol;
+      break;
+    }
+    // restart from the Ritz vector
+    HL_CUDA(cudaMemcpyAsync(vin, v_out, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return res;
+}
+
+}  // namespace hallar

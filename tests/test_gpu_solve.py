@@ -1,0 +1,130 @@
+"""GPU hallar_solve against closed-form SDP values and the oracle's solves.
+
+Every solve runs through the C ABI and must reach the relative KKT tolerance
+of eq. termination2; its objective must match the closed form (or the
+oracle's stored value) to the tolerance.  Both precision forms are checked.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hallar_oracle as O  # noqa: E402
+from paper_2505_13719_b300 import instances as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "solve_values.json")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_13719_b300 import hallar
+    return hallar
+
+
+def gpu_solve(H, inst, r0, seed, prec=0, tol=1e-6, **opts):
+    dt = np.float32 if prec else np.float64
+    U0 = I.initial_factor(inst.n, r0, seed).astype(dt)
+    with H.create_from_instance(inst, prec, tol=tol, **opts) as hd:
+        st, res = H.hallar_solve(hd.h, U0, r0)
+        rank = H.hallar_get_solution(hd.h)
+        U = np.empty((inst.n, rank), dtype=dt)
+        p = np.empty(inst.m)
+        H.hallar_get_solution(hd.h, U, rank, p)
+    return st, res, U.astype(np.float64), p
+
+
+CLOSED = [
+    ("maxcut K8", lambda: I.maxcut(8, *I.complete_graph(8)), 16.0),
+    ("maxcut C7", lambda: I.maxcut(7, *I.cycle_graph(7)), 3.5 * (1 + math.cos(math.pi / 7))),
+    ("maxcut C101", lambda: I.maxcut(101, *I.cycle_graph(101)),
+     50.5 * (1 + math.cos(math.pi / 101))),
+    ("maxcut torus 32x32 unit", lambda: I.maxcut_torus(32, "unit"), 2048.0),
+    ("theta C5", lambda: I.theta(5, *I.cycle_graph(5)), math.sqrt(5.0)),
+    ("theta C9", lambda: I.theta(9, *I.cycle_graph(9)),
+     9 * math.cos(math.pi / 9) / (1 + math.cos(math.pi / 9))),
+    ("theta K6", lambda: I.theta(6, *I.complete_graph(6)), 1.0),
+    ("theta empty 7", lambda: I.theta(7, np.zeros(0, int), np.zeros(0, int)), 7.0),
+    ("theta H(10,2)", lambda: I.theta(1024, *I.hypercube_graph(10)), 512.0),
+]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,make,ref", CLOSED, ids=[c[0] for c in CLOSED])
+def test_closed_form(H, name, make, ref, prec):
+    inst = make()
+    st, res, U, p = gpu_solve(H, inst, 2, 7, prec=prec, tol=1e-6)
+    assert st == H.HALLAR_OK, res.as_dict()
+    assert res.kkt <= 1e-6
+    val = inst.sense * res.pval
+    assert abs(val - ref) <= 1e-5 * abs(ref), (val, ref)
+    assert np.linalg.norm(U) <= math.sqrt(inst.tau2) * (1 + 1e-6)
+
+
+def test_matrix_completion(H):
+    inst = I.completion(60, 80, 2, I.completion_sample_count(60, 80, 2) // 4, seed=5)
+    st, res, U, p = gpu_solve(H, inst, 2, 9, tol=1e-6)
+    assert st == H.HALLAR_OK
+    nuc = inst.meta["nuclear_norm"]
+    assert abs(res.pval - nuc) <= 1e-4 * nuc
+    M = inst.meta["G"] @ inst.meta["H"].T
+    X12 = U[:60] @ U[60:].T
+    assert np.linalg.norm(X12 - M) <= 1e-2 * np.linalg.norm(M)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solution_certificate_small(H, prec):
+    # the returned (U, p, theta): KKT residuals recomputed by the oracle and
+    # S = C + A*p + theta I psd by a dense eigenvalue
+    inst = I.maxcut(60, *I.er_graph(60, 0.15, 4))
+    st, res, U, p = gpu_solve(H, inst, 3, 5, prec=prec, tol=1e-6)
+    assert st == H.HALLAR_OK
+    pval, dval, rp, rg, rd = O.kkt_measures(inst, U, p, res.theta, 0.0, O.c_norm1(inst))
+    assert max(rp, rg) <= 2e-6
+    G = O.adjoint_matrix(inst, np.concatenate([[1.0], p]))[0].toarray() + res.theta * np.eye(inst.n)
+    assert np.linalg.eigvalsh(G)[0] >= -1e-5 * (1 + O.c_norm1(inst))
+
+
+STORED = {
+    "maxcut_er_n1000_p0.01": lambda: I.maxcut_er_1000(seed=1),
+    "maxcut_torus_24x24_pm1": lambda: I.maxcut_torus(24, "pm1", seed=2),
+    "theta_gnm_n300_m1500": lambda: I.theta_gnm(300, 1500, seed=3),
+}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", sorted(STORED))
+def test_against_stored_oracle_solve(H, name, prec):
+    if not os.path.exists(GOLDEN):
+        pytest.skip("stored oracle values not generated")
+    ref = json.load(open(GOLDEN))[name]
+    inst = STORED[name]()
+    st, res, U, p = gpu_solve(H, inst, ref["r0"], ref["u0_seed"], prec=prec, tol=1e-6)
+    assert st == H.HALLAR_OK, res.as_dict()
+    assert abs(res.pval - ref["pval"]) <= 1e-5 * abs(ref["pval"]), (res.pval, ref["pval"])
+
+
+def test_solve_against_oracle_solve(H):
+    inst = I.theta(40, *I.er_graph(40, 0.2, 8))
+    U0 = I.initial_factor(inst.n, 3, 10)
+    ores = O.hallar_solve(inst, U0, opt=O.Options(tol=1e-7))
+    st, res, U, p = gpu_solve(H, inst, 3, 10, tol=1e-7)
+    assert st == H.HALLAR_OK
+    assert abs(res.pval - ores.pval) <= 1e-6 * abs(ores.pval)
+
+
+def test_limits_report_status(H):
+    inst = I.maxcut_er_1000(seed=1)
+    U0 = I.initial_factor(inst.n, 10, 1001)
+    with H.create_from_instance(inst, max_outer=1) as hd:
+        st, res = H.hallar_solve(hd.h, U0, 10)
+    assert st == H.HALLAR_ENOTCONV and res.outer_iters == 1
+    with H.create_from_instance(inst, time_limit_s=1e-3) as hd:
+        st, res = H.hallar_solve(hd.h, U0, 10)
+    assert st == H.HALLAR_ETIMEOUT
