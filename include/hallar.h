@@ -92,7 +92,7 @@ typedef struct {
   double beta_max;        /* cap of the penalty schedule (1e8)                    */
   double eps_decay;       /* epsilon_{t+1} = eps_decay * epsilon_t (0.5)          */
   double eps1_rel;        /* epsilon_1 = eps1_rel (1 + tau^2 ||C||_1) (1e-2)      */
-  double lanczos_tol_rel; /* Ritz residual tolerance = this * epsilon_t / tau^2   */
+  double lanczos_tol_rel; /* Ritz residual tol = this * epsilon_t / tau^2 (0.5)   */
   double time_limit_s;    /* wall-clock limit of hallar_solve (3600)              */
   int32_t r_cap;          /* maximum factor rank; the Gram trim keeps r_cap (32)  */
   int32_t max_outer;      /* AL iterations (300)                                  */
@@ -187,6 +187,19 @@ hallar_status hallar_solve(hallar_t h, const void* U0, int32_t r0, const double*
  * may be NULL; rank (host) receives the rank when non-NULL. */
 hallar_status hallar_get_solution(hallar_t h, void* U, int32_t r_capacity, double* p,
                                   int32_t* rank);
+
+/* Kernel timing.  Kernel classes: 0 = the fused constraint map + shift +
+ * SpMM (hallar_grad, and every gradient of hallar_solve), 1 = the
+ * value-change kernel of the ADAP-FISTA / ADAP-AIPP tests, 2 = the Lanczos
+ * basis passes.  op = 1 clears the counters and starts timing (a CUDA event
+ * pair on the handle's stream around every launch of those kernels), op = 2
+ * stops timing, op = 0 only reads.  ms[3], launches[3] and bytes[3] (host,
+ * may be NULL) receive, per class since the last clear, the summed kernel
+ * milliseconds, the launch counts and the summed algorithmic bytes (every
+ * input array read once and every output written once; gathered neighbour
+ * rows are not counted).  Timing adds two event records per launch. */
+hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launches,
+                             double* bytes);
 
 /* Problem sizes of a handle (host pointers; any may be NULL). */
 hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz_merged,

@@ -347,7 +347,7 @@ class Options:
     max_aipp: int = 20000
     max_fista: int = 400
     lanczos_kmax: int = 300
-    lanczos_tol_rel: float = 1e-2
+    lanczos_tol_rel: float = 0.5
     r_cap: int = 64
     seed: int = 0
     time_limit_s: float = 3600.0
@@ -581,7 +581,9 @@ def hallar_solve(inst, U0, p0=None, opt: Options | None = None, log=None):
       the nonconvex solver gets rho_t = epsilon_t / tau so that
       <R, Y> <= epsilon_t on the ball (Alg. 1 step 6 passes epsilon_t).
     * beta_t: start at beta0; after each dual update, double beta (capped at
-      beta_max) when ||r_t|| > ||r_{t-1}|| / 4 (a LANCELOT-style test).
+      beta_max) when ||r_t|| > ||r_{t-1}|| / 4 while the relative primal
+      infeasibility is still above tol (a LANCELOT-style test: the penalty
+      grows only while infeasibility is the obstacle).
     * termination: eq. termination2 at relative tolerance tol.
     * U0 outside the ball is projected onto it.
     """
@@ -646,7 +648,7 @@ def hallar_solve(inst, U0, p0=None, opt: Options | None = None, log=None):
             res = (pval, dval, rp, rg, rd, True)
             break
         rnorm = float(np.linalg.norm(r))
-        if rnorm > 0.25 * prev_rnorm:
+        if rp > opt.tol and rnorm > 0.25 * prev_rnorm:
             beta = min(2.0 * beta, opt.beta_max)
         prev_rnorm = rnorm
         if time.perf_counter() - t0 > opt.time_limit_s:

@@ -31,12 +31,48 @@ void* ensure_buffer(Ctx* c, void** buf, size_t* cur, size_t bytes) {
   return *buf;
 }
 
-void sync(Ctx* c) { HL_CUDA(cudaStreamSynchronize(c->stream)); }
+void sync(Ctx* c) {
+  HL_CUDA(cudaStreamSynchronize(c->stream));
+  if (!c->prof_pending.empty()) prof_resolve(c);
+}
 
 void fetch_scalars(Ctx* c, int first, int count) {
   HL_CUDA(cudaMemcpyAsync(c->h_scal + first, c->d_scal + first, count * sizeof(double),
                           cudaMemcpyDeviceToHost, c->stream));
   sync(c);
+}
+
+int prof_begin(Ctx* c, int cls, double bytes) {
+  if (!c->prof_on) return -1;
+  c->prof_bytes[cls] += bytes;
+  // the pool is reused: pending pair q uses events 2q and 2q + 1
+  const size_t idx = c->prof_pending.size();  // two entries per pending pair
+  while (c->prof_pool.size() < idx + 2) {
+    cudaEvent_t e;
+    HL_CUDA(cudaEventCreate(&e));
+    c->prof_pool.push_back(e);
+  }
+  HL_CUDA(cudaEventRecord(c->prof_pool[idx], c->stream));
+  c->prof_pending.push_back(cls);
+  c->prof_pending.push_back((int)idx);
+  return (int)idx;
+}
+
+void prof_end(Ctx* c, int token) {
+  if (token < 0) return;
+  HL_CUDA(cudaEventRecord(c->prof_pool[token + 1], c->stream));
+}
+
+void prof_resolve(Ctx* c) {
+  for (size_t q = 0; q + 1 < c->prof_pending.size(); q += 2) {
+    const int cls = c->prof_pending[q], idx = c->prof_pending[q + 1];
+    float ms = 0.0f;
+    HL_CUDA(cudaEventSynchronize(c->prof_pool[idx + 1]));
+    HL_CUDA(cudaEventElapsedTime(&ms, c->prof_pool[idx], c->prof_pool[idx + 1]));
+    c->prof_ms[cls] += ms;
+    c->prof_n[cls] += 1;
+  }
+  c->prof_pending.clear();
 }
 
 namespace {
@@ -305,6 +341,7 @@ void release(Ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   for (void* p : c->owned) cudaFree(p);
   c->owned.clear();
   if (c->h_scal) cudaFreeHost(c->h_scal);
@@ -330,7 +367,7 @@ hallar_status hallar_default_options(hallar_options* o) {
   o->beta_max = 1e8;
   o->eps_decay = 0.5;
   o->eps1_rel = 1e-2;
-  o->lanczos_tol_rel = 1e-2;
+  o->lanczos_tol_rel = 0.5;
   o->time_limit_s = 3600.0;
   o->r_cap = 32;
   o->max_outer = 300;
@@ -558,6 +595,32 @@ hallar_status hallar_get_solution(hallar_t h, void* U, int32_t r_capacity, doubl
     }
     if (p) copy_out_dvec(c, p, c->sol_p, c->P.m);
     sync(c);
+    return HALLAR_OK;
+  });
+}
+
+hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launches,
+                             double* bytes) {
+  return guarded(h, [&]() -> hallar_status {
+    Ctx* c = h;
+    if (op < 0 || op > 2) fail(HALLAR_EINVAL, "hallar_profile: op must be 0, 1 or 2");
+    sync(c);
+    if (ms)
+      for (int k = 0; k < 3; ++k) ms[k] = c->prof_ms[k];
+    if (launches)
+      for (int k = 0; k < 3; ++k) launches[k] = c->prof_n[k];
+    if (bytes)
+      for (int k = 0; k < 3; ++k) bytes[k] = c->prof_bytes[k];
+    if (op == 1) {
+      for (int k = 0; k < 3; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+        c->prof_bytes[k] = 0.0;
+      }
+      c->prof_on = true;
+    } else if (op == 2) {
+      c->prof_on = false;
+    }
     return HALLAR_OK;
   });
 }

@@ -99,6 +99,13 @@ struct hallar_ctx {
   void* lan_w = nullptr; size_t lan_w_bytes = 0;
   void* lan_part = nullptr; size_t lan_part_bytes = 0;
   void* lan_h = nullptr; size_t lan_h_bytes = 0;
+  // kernel timing (hallar_profile): event pairs pending per kernel class
+  bool prof_on = false;
+  double prof_ms[3] = {0.0, 0.0, 0.0};
+  double prof_bytes[3] = {0.0, 0.0, 0.0};  // algorithmic bytes of the timed launches
+  int64_t prof_n[3] = {0, 0, 0};
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<int> prof_pending;  // (class, start event index), stop = start + 1
   // buffers of the last solve (freed by the next solve or by destroy)
   std::vector<void*> solve_bufs;
   void* sol_U = nullptr; int sol_rank = 0; int sol_ld = 0;
@@ -147,6 +154,11 @@ void dfree(Ctx* c, void* p);
 // grow *buf to at least `bytes` (contents not kept)
 void* ensure_buffer(Ctx* c, void** buf, size_t* cur_bytes, size_t bytes);
 void sync(Ctx* c);
+// kernel timing: prof_begin records a start event and returns its token (or
+// -1 when timing is off); prof_end records the stop event of that token
+int prof_begin(Ctx* c, int cls, double bytes);
+void prof_end(Ctx* c, int token);
+void prof_resolve(Ctx* c);  // after a stream sync: add finished pairs
 void fetch_scalars(Ctx* c, int first, int count);  // d_scal -> h_scal, then sync
 
 // element size of a factor array for this handle
@@ -169,11 +181,14 @@ struct GradOut {
   double* T = nullptr;      // [m+1] or null (T[0] and the trace row by the caller)
 };
 
+// algorithmic bytes of one launch of the fused operator (see kernels_ops.cu)
+double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool reads_p);
 // pre-pass: colsum of U into colsum_out, S_PRE[0] = |U|_F^2, S_PRE[1] = |colsum|^2
 void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot);
 // fused A~(UU^T), shift and SpMM.  Reductions into S_GRAD:
 //   [0] C.UU^T without the C_J part, [1] sum p_l r_l, [2] sum r_l^2 (the
-//   trace row excluded).
+//   trace row excluded), [3] sum |p'_l| |A_l.UU^T| + |sparse and diagonal
+//   C terms| (the scale of the rounding of g).
 void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double beta,
                  const double* colsum, GradOut out);
 // g(Y) - g(X) pieces into S_DIFF: [0] dT0 (no C_J part) [1] p.dT [2] dT(2rX+dT)

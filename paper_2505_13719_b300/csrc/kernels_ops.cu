@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       cj[k][v] = (io.colsum != nullptr && c < a.ld) ? (T)(a.C_J * io.colsum[c]) : (T)0;
     }
 
-  double red[3] = {0.0, 0.0, 0.0};  // C.UU^T (sparse + diagonal part), p.r, r.r
+  // C.UU^T (sparse + diagonal part), p.r, r.r, and the magnitude
+  // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g
+  double red[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
     T u[K][VEC], acc[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
@@ -118,6 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       if (lane_g == 0) {
         red[1] += pi * r;
         red[2] += r * r;
+        red[3] += fabs(pi + a.beta * r) * (double)nrm;
         if (io.resid) io.resid[i] = r;
         if (io.Tout) io.Tout[i] = (double)nrm;
       }
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
           if (owner && lane_g == 0) {
             red[1] += pl * r;
             red[2] += r * r;
+            red[3] += fabs(pl + a.beta * r) * fabs((double)dot);
             if (io.resid) io.resid[l] = r;
             if (io.Tout) io.Tout[l] = (double)dot;
           }
@@ -180,7 +184,11 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
         }
     }
     red[0] += (double)cdot_l;
-    if (lane_g == 0) red[0] += a.cdiag[i] * (double)nrm;
+    red[3] += fabs((double)cdot_l);
+    if (lane_g == 0) {
+      red[0] += a.cdiag[i] * (double)nrm;
+      red[3] += fabs(a.cdiag[i]) * (double)nrm;
+    }
 
     if (W != nullptr) {
       const T dc = (T)dcoef;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       }
     }
   }
-  grid_reduce<3>(red, a.partials, a.counter, a.out);
+  grid_reduce<4>(red, a.partials, a.counter, a.out);
 }
 
 // ---------------------------------------------------------------------------
@@ -498,6 +506,20 @@ Shape pick_shape(int ld, int vec) {
 
 }  // namespace
 
+// algorithmic bytes of one operator launch: the factor row (and W) once, the
+// merged CSR once, the per-row and per-constraint vectors once
+double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool reads_p) {
+  const Problem& P = c->P;
+  const double es = (double)elem_size(c);
+  double b = (double)P.n * ld * es * (writes_w ? 2.0 : 1.0);
+  b += (double)P.nnz * 4.0;                                      // column indices
+  if (P.code) b += (double)P.nnz * 4.0;                          // constraint codes
+  if (P.fam != FAM_EDGE) b += (double)P.nnz * es;                // C values
+  b += (double)(P.n + 1) * 4.0 + (double)P.n * 8.0;              // row pointers, diagonal
+  b += (double)P.m * 8.0 * (1.0 + (reads_p ? 1.0 : 0.0) + (writes_resid ? 1.0 : 0.0));  // b, p, r
+  return b;
+}
+
 void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double beta,
                  const double* colsum, GradOut out) {
   (void)r;
@@ -512,11 +534,13 @@ void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double b
   io.W = out.W;
   io.resid = out.resid;
   io.Tout = out.T ? out.T + 1 : nullptr;
+  const int tok = prof_begin(c, 0, op_bytes(c, ld, out.W != nullptr, out.resid != nullptr, true));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
     const int grid = grid_for(c, a.n, kBlock / G);
     k_grad<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
   }));
   HL_CHECK_LAUNCH(c);
+  prof_end(c, tok);
 }
 
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const double* p,
@@ -525,11 +549,14 @@ void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, co
   OpArgs a = make_args(c, ld, S_DIFF);
   a.p = p;
   DiffIO io{X, Y, rX, rY};
+  const int tok = prof_begin(c, 1, op_bytes(c, ld, false, rY != nullptr, true) +
+                                       (double)c->P.n * ld * (double)elem_size(c));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
     const int grid = grid_for(c, a.n, kBlock / G);
     k_value_change<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
   }));
   HL_CHECK_LAUNCH(c);
+  prof_end(c, tok);
 }
 
 void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot) {

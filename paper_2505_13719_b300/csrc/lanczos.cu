@@ -432,20 +432,26 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
     int kk = 0;
     for (int k = 0; k < kmax; ++k) {
       const int ncols = k + 1;
+      const int tok1 = prof_begin(c, 2, 8.0 * n * k + 24.0 * n + 16.0 * (double)c->P.nnz);
       HL_BY_NACC(ncols, k_lan_spmv<NACC><<<grid, kBlock, 0, c->stream>>>(
                             a, cur_in, vscale, vsum, Q, kcap, k, cur_w, part));
       HL_CHECK_LAUNCH(c);
+      prof_end(c, tok1);
       k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h);
       HL_CHECK_LAUNCH(c);
+      const int tok2 = prof_begin(c, 2, 8.0 * n * ncols + 16.0 * n);
       HL_BY_NACC(ncols, k_lan_orth<NACC><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, ncols, h,
                                                                           cur_w, part));
       HL_CHECK_LAUNCH(c);
+      prof_end(c, tok2);
       k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h2);
       HL_CHECK_LAUNCH(c);
+      const int tok3 = prof_begin(c, 2, 8.0 * n * ncols + 16.0 * n);
       HL_BY_NACC(ncols, k_lan_final<NACC><<<grid, kBlock, 0, c->stream>>>(
                             n, Q, kcap, ncols, h2, cur_w, c->red.partials, c->red.counter,
                             c->d_scal + S_LAN));
       HL_CHECK_LAUNCH(c);
+      prof_end(c, tok3);
       HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 2, h + k, sizeof(double),
                               cudaMemcpyDeviceToHost, c->stream));
       HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 3, h2 + k, sizeof(double),

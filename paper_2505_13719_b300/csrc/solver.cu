@@ -6,10 +6,16 @@
 // open points are the same as the oracle's:
 //   * epsilon_t = max(tol/2 (1 + |pval|), eps_1 eps_decay^(t-1)),
 //     eps_1 = eps1_rel (1 + tau^2 ||C||_1); ADAP-AIPP gets rho = epsilon_t / tau;
-//   * beta doubles (<= beta_max) when ||r_t|| > ||r_{t-1}|| / 4;
+//   * beta doubles (<= beta_max) when ||r_t|| > ||r_{t-1}|| / 4 while the
+//     relative primal infeasibility is above tol;
 //   * ADAP-AIPP: M_j = max(1, Mbar_{j-1}/2), lambda carried across calls;
 //   * ADAP-FISTA: linearisation test with g(y) - g(x~) formed as a
 //     difference; V = grad psi(y) - grad psi(x~) + L (x~ - y);
+//   * floating point: the step-2 tests of ADAP-FISTA and ADAP-AIPP accept a
+//     violation up to 16 u lam sum|terms of g| (u the unit roundoff of the
+//     stored factor), and ADAP-AIPP stops when a prox step leaves W
+//     unchanged; neither is in the paper, and in FP64 both are inert in
+//     practice;
 //   * Lanczos start: the previous eigenvector plus 0.1/sqrt(n) times a
 //     SplitMix64 vector, Ritz residual <= lanczos_tol_rel epsilon_t / tau^2;
 //   * theta = 0: no zero column is appended; rank above r_cap: keep the
@@ -75,7 +81,7 @@ void jacobi_eig(std::vector<double>& A, int r, std::vector<double>& V, std::vect
 }
 
 struct GradScal {
-  double T0 = 0, pr = 0, rr = 0, nrm2 = 0, g = 0;
+  double T0 = 0, pr = 0, rr = 0, nrm2 = 0, g = 0, mag = 0;
 };
 
 struct Solver {
@@ -97,6 +103,11 @@ struct Solver {
   explicit Solver(Ctx* cc) : c(cc), P(cc->P), o(cc->opt) {}
 
   double tau() const { return std::sqrt(P.tau2); }
+  // unit roundoff of the stored factor: rounding the iterates moves g by up
+  // to about u * mag; the acceptance tests of ADAP-FISTA step 2 and
+  // ADAP-AIPP step 2 allow kRoundSlack times that
+  double unit() const { return o.precision == HALLAR_MIXED ? 0x1p-24 : 0x1p-53; }
+  static constexpr double kRoundSlack = 16.0;
   void* fbuf() { return dalloc<unsigned char>(c, fbytes); }
 
   void setup() {
@@ -140,10 +151,12 @@ struct Solver {
     s.T0 = h[S_GRAD] + P.C_J * h[S_PRE + 1];
     s.pr = h[S_GRAD + 1];
     s.rr = h[S_GRAD + 2];
+    s.mag = h[S_GRAD + 3] + std::fabs(P.C_J) * h[S_PRE + 1];
     if (P.has_trace) {
       const double rt = s.nrm2 - b_tr;
       s.pr += p_tr * rt;
       s.rr += rt * rt;
+      s.mag += std::fabs(p_tr + beta * rt) * s.nrm2;
     }
     s.g = s.T0 + s.pr + 0.5 * beta * s.rr;
     return s;
@@ -188,6 +201,7 @@ struct Solver {
     const double tauv = tau();
     for (int it = 0; it < o.max_fista; ++it) {
       R.fista_iters++;
+      if ((it & 15) == 15) check_time();
       double Ln = L, a = 0.0, d2 = 0.0, dy0 = 0.0;
       for (;;) {                                                 // step 2
         a = (tk + std::sqrt(tk * tk + 4.0 * tk * A * (Ln - mu))) / (2.0 * (Ln - mu));
@@ -204,9 +218,13 @@ struct Solver {
         const double dlin = c->h_scal[S_VEC + 2];
         dy0 = c->h_scal[S_VEC + 3];
         const double dpsi = lamv * change_read(nrm_xt2) + dlin;
+        const double slack = kRoundSlack * unit() * lamv * grad_read().mag;
         if (!std::isfinite(dpsi) || !std::isfinite(gd))
           throw Err{HALLAR_ENUMERIC, "non-finite ADAP-FISTA step"};
-        if (gd + (1.0 - o.chi) * Ln / 4.0 * d2 >= dpsi) break;
+        if (o.verbose >= 3)
+          std::fprintf(stderr, "[fista] it=%d L=%.3e d2=%.3e gd=%.6e dpsi=%.6e dy0=%.3e\n", it, Ln,
+                       d2, gd, dpsi, dy0);
+        if (gd + (1.0 - o.chi) * Ln / 4.0 * d2 >= dpsi - slack) break;
         Ln *= 2.0;
         if (Ln > 1e30) {
           R.fista_failures++;
@@ -243,6 +261,7 @@ struct Solver {
       R.aipp_iters++;
       check_time();
       double L = 1.0, VmD2 = 0.0;
+      bool stalled = false;
       GradScal gy;
       for (;;) {
         const double Mlow = std::fmax(1.0, Mbar / 2.0);            // step 1
@@ -256,7 +275,12 @@ struct Solver {
           const double VD = c->h_scal[S_VEC2];
           const double D2 = c->h_scal[S_VEC2 + 1];
           VmD2 = c->h_scal[S_VEC2 + 2];
-          if (-lam * dg - 0.5 * D2 >= -VD) break;                   // step 2
+          if (o.verbose >= 2)
+            std::fprintf(stderr, "[aipp] j=%d lam=%.3e L=%.3e dg=%.6e D2=%.3e VD=%.6e |R|=%.3e rho=%.3e\n",
+                         j, lam, L, dg, D2, VD, std::sqrt(VmD2) / lam, rho);
+          const double slack = kRoundSlack * unit() * lam * gy.mag;
+          stalled = D2 == 0.0;
+          if (stalled || -lam * dg - 0.5 * D2 >= -VD - slack) break;  // step 2
         }
         lam /= 2.0;
         if (lam < 1e-30) throw Err{HALLAR_ENUMERIC, "ADAP-AIPP: prox stepsize underflow"};
@@ -266,7 +290,9 @@ struct Solver {
       std::swap(ctr, ynew);  // the accepted point is the next prox centre
       std::swap(r_ctr, rY);
       nrm_ctr2 = gy.nrm2;
-      if (Rn <= rho || j + 1 == o.max_aipp) {                       // step 3
+      // step 3; a prox step that left W unchanged (below the resolution of
+      // the stored factor) cannot make further progress: stop there too
+      if (Rn <= rho || stalled || j + 1 == o.max_aipp) {
         std::swap(Ytil, ctr);
         std::swap(rY, r_ctr);
         *gs = gy;
@@ -426,7 +452,8 @@ struct Solver {
         R.converged = 1;
         break;
       }
-      if (rnorm > 0.25 * prev_rnorm) beta = std::fmin(2.0 * beta, o.beta_max);
+      // the penalty grows only while primal infeasibility is above the tolerance
+      if (rp > o.tol && rnorm > 0.25 * prev_rnorm) beta = std::fmin(2.0 * beta, o.beta_max);
       prev_rnorm = rnorm;
       pval_now = pval;
       check_time();

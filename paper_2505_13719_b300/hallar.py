@@ -25,7 +25,7 @@ FAMILY = {"diag": HALLAR_DIAG, "edge": HALLAR_EDGE, "observed": HALLAR_OBSERVED}
 
 EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_grad",
             "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
-            "hallar_destroy", "hallar_last_error", "hallar_status_string")
+            "hallar_destroy", "hallar_last_error", "hallar_status_string", "hallar_profile")
 
 
 class hallar_options(C.Structure):
@@ -71,6 +71,7 @@ def _load():
         "hallar_solve": ([P, P, I32, P, P], C.c_int),
         "hallar_get_solution": ([P, P, I32, P, P], C.c_int),
         "hallar_get_sizes": ([P, P, P, P, P], C.c_int),
+        "hallar_profile": ([P, I32, P, P, P], C.c_int),
         "hallar_destroy": ([P], None),
         "hallar_last_error": ([P], C.c_char_p),
         "hallar_status_string": ([C.c_int], C.c_char_p),
@@ -183,6 +184,17 @@ def hallar_get_sizes(h):
     prec = C.c_int32()
     _check(_lib.hallar_get_sizes(h, C.byref(n), C.byref(m), C.byref(nnz), C.byref(prec)), h)
     return n.value, m.value, nnz.value, prec.value
+
+
+def hallar_profile(h, op):
+    """op 1: clear and start kernel timing, 2: stop, 0: read.  Returns
+    (ms[3], launches[3], bytes[3]) for the fused operator, value-change and
+    Lanczos kernel classes."""
+    ms = (C.c_double * 3)()
+    nl = (C.c_int64 * 3)()
+    by = (C.c_double * 3)()
+    _check(_lib.hallar_profile(h, int(op), ms, nl, by), h)
+    return list(ms), list(nl), list(by)
 
 
 def hallar_destroy(h):
