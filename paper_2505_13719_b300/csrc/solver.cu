@@ -108,7 +108,15 @@ struct Solver {
   // ADAP-AIPP step 2 allow kRoundSlack times that
   double unit() const { return o.precision == HALLAR_MIXED ? 0x1p-24 : 0x1p-53; }
   static constexpr double kRoundSlack = 16.0;
-  void* fbuf() { return dalloc<unsigned char>(c, fbytes); }
+  // the solver's own buffers (kept after the solve for hallar_get_solution)
+  std::vector<void*> mine;
+  template <class T>
+  T* salloc(size_t count) {
+    T* q = dalloc<T>(c, count);
+    mine.push_back(q);
+    return q;
+  }
+  void* fbuf() { return salloc<unsigned char>(fbytes); }
 
   void setup() {
     n = P.n;
@@ -117,15 +125,15 @@ struct Solver {
     fbytes = (size_t)n * ld_max * elem_size(c);
     Ytil = fbuf(); ctr = fbuf(); x = fbuf(); y = fbuf(); xt = fbuf(); z = fbuf();
     ynew = fbuf(); Wg = fbuf(); Wy = fbuf(); tmp = fbuf();
-    p = dalloc<double>(c, m);
-    r_ctr = dalloc<double>(c, m);
-    rX = dalloc<double>(c, m);
-    rY = dalloc<double>(c, m);
-    pshift = dalloc<double>(c, m);
-    v = dalloc<double>(c, n);
-    vprev = dalloc<double>(c, n);
-    v0 = dalloc<double>(c, n);
-    gram = dalloc<double>(c, (size_t)ld_max * ld_max);
+    p = salloc<double>(m);
+    r_ctr = salloc<double>(m);
+    rX = salloc<double>(m);
+    rY = salloc<double>(m);
+    pshift = salloc<double>(m);
+    v = salloc<double>(n);
+    vprev = salloc<double>(n);
+    v0 = salloc<double>(n);
+    gram = salloc<double>((size_t)ld_max * ld_max);
     if (P.has_trace) HL_CUDA(cudaMemcpy(&b_tr, P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
   }
 
@@ -477,12 +485,9 @@ hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_res
   c->solve_bufs.clear();
   c->sol_U = nullptr;
   c->sol_p = nullptr;
-  const size_t before = c->owned.size();
   const int64_t launches0 = c->launches;
   Solver s(c);
-  auto keep_buffers = [&]() {
-    for (size_t i = before; i < c->owned.size(); ++i) c->solve_bufs.push_back(c->owned[i]);
-  };
+  auto keep_buffers = [&]() { c->solve_bufs = s.mine; };
   try {
     s.setup();
     const hallar_status st = s.run(U0, r0, p0, res);

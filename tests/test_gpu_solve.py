@@ -135,3 +135,16 @@ def test_limits_report_status(H):
     with H.create_from_instance(inst, time_limit_s=1e-3) as hd:
         st, res = H.hallar_solve(hd.h, U0, 10)
     assert st == H.HALLAR_ETIMEOUT
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_repeated_solves_on_one_handle(H, prec):
+    # a handle keeps its Lanczos workspace across solves; each solve frees
+    # only its own buffers, so back-to-back solves give identical results
+    inst = I.theta(64, *I.er_graph(64, 0.1, 3))
+    dt = np.float32 if prec else np.float64
+    U0 = I.initial_factor(inst.n, 2, 4).astype(dt)
+    with H.create_from_instance(inst, prec, tol=TOLS[prec]) as hd:
+        out = [H.hallar_solve(hd.h, U0, 2) for _ in range(3)]
+    assert all(st == H.HALLAR_OK for st, _ in out)
+    assert out[0][1].pval == out[1][1].pval == out[2][1].pval
