@@ -157,6 +157,7 @@ class GradResult:
     resid: np.ndarray   # r = A(UU^T) - b
     pshift: np.ndarray  # p' = p + beta r
     T: np.ndarray       # A~(UU^T)
+    mag: float = 0.0    # sum |p'_l| |T_l| + sum |C terms|: the scale of g's rounding
 
 
 def al_grad(inst, U, p, beta):
@@ -168,7 +169,28 @@ def al_grad(inst, U, p, beta):
     g = T[0] + float(p @ r) + 0.5 * beta * float(r @ r)
     ps = p + beta * r
     W = adjoint_apply(inst, np.concatenate([[1.0], ps]), U)
-    return GradResult(g=g, W=W, resid=r, pshift=ps, T=T)
+    return GradResult(g=g, W=W, resid=r, pshift=ps, T=T, mag=_magnitude(inst, U, ps, T))
+
+
+def _magnitude(inst, U, ps, T):
+    """sum_l |p'_l| |A_l.UU^T| plus the absolute values of the terms of
+    C.UU^T: the size of the terms whose rounding perturbs g."""
+    a, b, v = cost_entries(inst)
+    mag = float(np.abs(ps) @ np.abs(T[1:]))
+    if v.shape[0]:
+        mag += float(np.abs(v) @ np.abs(_pair_dots(U, a, b)))
+    if inst.C_J != 0.0:
+        s = U.sum(axis=0)
+        mag += abs(inst.C_J) * float(s @ s)
+    if inst.C_I != 0.0:
+        mag += abs(inst.C_I) * float(np.sum(U * U))
+    return mag
+
+
+# unit roundoff of float64 and the multiple of it that the ADAP-FISTA and
+# ADAP-AIPP step-2 tests allow (times lambda and the magnitude of g's terms)
+UNIT_ROUNDOFF = 2.0 ** -53
+ROUND_SLACK = 16.0
 
 
 def al_value(inst, U, p, beta):
@@ -420,7 +442,9 @@ def adap_fista(sub, lam, center, mu, L0, opt, tau):
             d = ynew - xt
             dg, _ry = sub.change(xt, ynew, gr.resid)
             dpsi = lam * dg + float(np.sum(d * (0.5 * (ynew + xt) - center)))
-            if float(np.sum(dpsi_xt * d)) + (1.0 - opt.chi) * Ln / 4.0 * float(np.sum(d * d)) >= dpsi:
+            slack = ROUND_SLACK * UNIT_ROUNDOFF * lam * gr.mag
+            if float(np.sum(dpsi_xt * d)) + (1.0 - opt.chi) * Ln / 4.0 * float(np.sum(d * d)) \
+                    >= dpsi - slack:
                 break
             Ln *= 2.0
             if Ln > 1e30:
@@ -439,7 +463,7 @@ def adap_fista(sub, lam, center, mu, L0, opt, tau):
             dpsi_y = lam * 2.0 * gy.W + (ynew - center)
             V = dpsi_y - dpsi_xt + Ln * (xt - ynew)
             dg0, _ = sub.change(center, ynew, None)
-            return "success", ynew, Ln, V, dg0
+            return "success", ynew, Ln, V, (dg0, gy.mag)
         y, A, tk, L = ynew, A_new, tk_new, Ln
     cnt.fista_fail += 1
     return "failure", None, L, None, None
@@ -457,6 +481,10 @@ def adap_aipp(sub, W0, rho, state, opt, tau):
 
     Reading: M_j = max(1, Mbar_{j-1} / 2) within the allowed [1, Mbar_{j-1}];
     lambda carries over between calls (it only ever halves, step 2).
+    Floating point: the step-2 inequality (and ADAP-FISTA's step-2 test)
+    accepts a violation up to ROUND_SLACK * UNIT_ROUNDOFF * lam * (sum of
+    the magnitudes of g's terms), the size of rounding in g; a prox step that
+    leaves W unchanged ends the method (no further progress is possible).
     The step-2 inequality lam g(W_{j-1}) - [lam g(W) + 1/2 ||W - W_{j-1}||^2]
     >= V . (W_{j-1} - W) is evaluated with g(W) - g(W_{j-1}) formed as a
     difference (al_value_change).
@@ -466,20 +494,25 @@ def adap_aipp(sub, W0, rho, state, opt, tau):
     R = np.zeros_like(W0)
     for _j in range(opt.max_aipp):
         cnt.aipp_iters += 1
+        stalled = False
         while True:
             Mlow = max(1.0, state.Mbar / 2.0)                          # step 1
-            st, W, L, V, dg = adap_fista(sub, state.lam, Wprev, 0.5, Mlow, opt, tau)
+            st, W, L, V, dgm = adap_fista(sub, state.lam, Wprev, 0.5, Mlow, opt, tau)
             if st == "success":
+                dg, mag = dgm
                 D = W - Wprev
-                lhs = -state.lam * dg - 0.5 * float(np.sum(D * D))
-                if lhs >= -float(np.sum(V * D)):                        # step 2
+                d2 = float(np.sum(D * D))
+                stalled = d2 == 0.0
+                lhs = -state.lam * dg - 0.5 * d2
+                slack = ROUND_SLACK * UNIT_ROUNDOFF * state.lam * mag
+                if stalled or lhs >= -float(np.sum(V * D)) - slack:     # step 2
                     break
             state.lam /= 2.0
             if state.lam < 1e-30:
                 raise RuntimeError("ADAP-AIPP: prox stepsize underflow")
         state.Mbar = L
         R = (V + Wprev - W) / state.lam                                 # eq. Rj def
-        if math.sqrt(float(np.sum(R * R))) <= rho:                      # step 3
+        if math.sqrt(float(np.sum(R * R))) <= rho or stalled:           # step 3
             return W, R
         Wprev = W                                                       # step 4
     return Wprev, R
