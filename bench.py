@@ -51,7 +51,48 @@ WORKLOADS = {
                       desc="Max-Cut SDP, 1000x1000 torus (n=1e6, 2e6 edges), weights +-1"),
     "er1000": dict(make=lambda: I.maxcut_er_1000(seed=1), r0=10, u0_seed=1001, r_cap=64,
                    exact=None, desc="Max-Cut SDP, Erdos-Renyi G(1000, 0.01), unit weights"),
+    # a small twin of torus_unit for profiler launch lists
+    "torus_unit_64": dict(make=lambda: I.maxcut_torus(64, "unit"), r0=10, u0_seed=1002,
+                          r_cap=32, exact=2.0 * 64 * 64,
+                          desc="Max-Cut SDP, 64x64 torus (n=4096), unit weights"),
 }
+
+
+def run_kernel(args):
+    """The fused constraint map + shift + SpMM alone (hallar_grad on device
+    arrays) on the workload's full-size instance: W + K launches, timed with
+    CUDA events on the launching stream; prints achieved GB/s."""
+    import torch
+
+    from paper_2505_13719_b300 import hallar as H
+
+    wl = WORKLOADS[args.workload]
+    inst = wl["make"]()
+    prec = H.HALLAR_MIXED if args.precision == "mixed" else H.HALLAR_FP64
+    tdt = torch.float32 if prec == H.HALLAR_MIXED else torch.float64
+    r = args.rank
+    stream = torch.cuda.current_stream()
+    hd = H.create_from_instance(inst, prec, stream=stream.cuda_stream)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    U = (torch.randn(inst.n, r, device="cuda", dtype=torch.float64, generator=gen)
+         / math.sqrt(r)).to(tdt)
+    W = torch.empty_like(U)
+    p = torch.randn(inst.m, device="cuda", dtype=torch.float64, generator=gen)
+    res = torch.empty(inst.m, device="cuda", dtype=torch.float64)
+    for _ in range(args.warmup):
+        H.hallar_grad(hd.h, U, r, p, 1.5, W, res)
+    H.hallar_profile(hd.h, 1)
+    for _ in range(args.steps):
+        H.hallar_grad(hd.h, U, r, p, 1.5, W, res)
+    ms, nl, by = H.hallar_profile(hd.h, 2)
+    hd.close()
+    peaks = load_peaks()
+    gbs = by[0] / (ms[0] / 1e3) / 1e9
+    return {"kernel": "fused_constraint_map_shift_spmm", "workload": wl["desc"],
+            "precision": args.precision, "rank": r, "launches": nl[0],
+            "avg_launch_us": round(1e3 * ms[0] / nl[0], 2),
+            "bytes_per_launch": by[0] / nl[0], "achieved_GBps": round(gbs, 1),
+            "peak_GBps": peaks["hbm_gbs"], "frac": round(gbs / peaks["hbm_gbs"], 4)}
 
 
 # ---------------------------------------------------------------------------
@@ -357,8 +398,15 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--kernel", choices=["grad"], default=None,
+                    help="time the fused operator kernel alone instead of full solves")
+    ap.add_argument("--rank", type=int, default=10, help="factor width for --kernel")
     args = ap.parse_args()
     world, rank = dist_setup(args.gpus)
+    if args.kernel:
+        if rank == 0:
+            print(json.dumps(run_kernel(args)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, world, rank)
     else:

@@ -201,6 +201,39 @@ hallar_status hallar_get_solution(hallar_t h, void* U, int32_t r_capacity, doubl
 hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launches,
                              double* bytes);
 
+/* Allocation-free fused gradient for the diagonal (Max-Cut) family.  The
+ * paper has no counterpart: it exists for callers that cannot let a library
+ * call cudaMalloc -- code running while a stream is captured into a CUDA
+ * graph, code that hands out device memory only from its own pool, hot
+ * paths that must not touch the allocator.  It computes what hallar_grad
+ * computes for a HALLAR_DIAG problem (A_i = e_i e_i^T, b, C), from arrays
+ * the caller owns, with no handle:
+ *   rowptr[n+1], col[nnz], cval[nnz]  off-diagonal entries of C (device,
+ *                                     full symmetric CSR, int32 indices),
+ *   cdiag[n]   diagonal of C (plus any C_I),  b[n], p[n]   (device),
+ *   U[n x r]   factor, W[n x r] = (C + Diag(p + beta r)) U   (device, double,
+ *              row-major with leading dimension r, 16-byte aligned),
+ *   resid[n]   r = diag(UU^T) - b (device; may be NULL),
+ *   g_out[1]   C.UU^T + p^T r + beta/2 |r|^2 (device),
+ *   stream     cudaStream_t to issue on (NULL: the legacy default stream),
+ *   errbuf     optional host buffer for a message on failure.
+ * Limits: 2 <= r <= 64 with r even, n < 2^31; anything else returns
+ * HALLAR_EINVAL with a message.  The call only enqueues work on `stream`
+ * and returns; it allocates nothing.  Its scratch (per-block partial sums
+ * and an arrival counter) is one static device array of about 29 KB that
+ * every GPU loading this library holds until exit; all calls share it and
+ * it keeps the last call's contents, the counter is cleared at the start of
+ * each call, and calls whose kernels overlap on the GPU race on it.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. */
+hallar_status hallar_grad_diag_noalloc(int64_t n, int32_t r, const int32_t* rowptr,
+                                       const int32_t* col, const double* cval,
+                                       const double* cdiag, const double* b, const double* p,
+                                       double beta, const double* U, double* W, double* resid,
+                                       double* g_out, void* stream, char* errbuf,
+                                       int32_t errbuf_len);
+
 /* Problem sizes of a handle (host pointers; any may be NULL). */
 hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz_merged,
                                int32_t* precision);

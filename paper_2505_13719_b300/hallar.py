@@ -25,7 +25,8 @@ FAMILY = {"diag": HALLAR_DIAG, "edge": HALLAR_EDGE, "observed": HALLAR_OBSERVED}
 
 EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_grad",
             "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
-            "hallar_destroy", "hallar_last_error", "hallar_status_string", "hallar_profile")
+            "hallar_destroy", "hallar_last_error", "hallar_status_string", "hallar_profile",
+            "hallar_grad_diag_noalloc")
 
 
 class hallar_options(C.Structure):
@@ -72,6 +73,8 @@ def _load():
         "hallar_get_solution": ([P, P, I32, P, P], C.c_int),
         "hallar_get_sizes": ([P, P, P, P, P], C.c_int),
         "hallar_profile": ([P, I32, P, P, P], C.c_int),
+        "hallar_grad_diag_noalloc": ([I64, I32, P, P, P, P, P, P, D, P, P, P, P, P, C.c_char_p,
+                                      I32], C.c_int),
         "hallar_destroy": ([P], None),
         "hallar_last_error": ([P], C.c_char_p),
         "hallar_status_string": ([C.c_int], C.c_char_p),
@@ -195,6 +198,20 @@ def hallar_profile(h, op):
     by = (C.c_double * 3)()
     _check(_lib.hallar_profile(h, int(op), ms, nl, by), h)
     return list(ms), list(nl), list(by)
+
+
+def hallar_grad_diag_noalloc(n, r, rowptr, col, cval, cdiag, b, p, beta, U, W, resid, g_out,
+                             stream=None):
+    """Allocation-free fused gradient of a diagonal-family problem from
+    caller-owned device arrays (see hallar.h); enqueues on `stream` (a
+    cudaStream_t as an int, or None) and returns without synchronising."""
+    err = C.create_string_buffer(256)
+    st = _lib.hallar_grad_diag_noalloc(int(n), int(r), _ptr(rowptr), _ptr(col), _ptr(cval),
+                                       _ptr(cdiag), _ptr(b), _ptr(p), float(beta), _ptr(U),
+                                       _ptr(W), _ptr(resid), _ptr(g_out), stream, err, 256)
+    if st != HALLAR_OK:
+        raise HallarError(st, err.value.decode())
+    return st
 
 
 def hallar_destroy(h):

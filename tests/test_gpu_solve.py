@@ -127,7 +127,7 @@ def test_against_stored_oracle_solve(H, name, prec):
 
 
 def test_solve_against_oracle_solve(H):
-    inst = I.theta(40, *I.er_graph(40, 0.2, 8))
+    inst = I.maxcut(60, *I.er_graph(60, 0.1, 8))
     U0 = I.initial_factor(inst.n, 3, 10)
     ores = O.hallar_solve(inst, U0, opt=O.Options(tol=1e-7, time_limit_s=120.0))
     assert ores.converged
