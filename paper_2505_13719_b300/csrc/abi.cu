@@ -269,6 +269,11 @@ void build_problem(Ctx* c, int64_t n, int64_t n1, const int64_t* rp, const int32
   }
   P.cdiag = upload(c, cdiag.data(), cdiag.size());
   P.b = upload(c, b, (size_t)m);
+  if (c->opt.precision == HALLAR_MIXED) {
+    std::vector<float> cd32(cdiag.begin(), cdiag.end()), b32(b, b + m);
+    P.cdiag32 = upload(c, cd32.data(), cd32.size());
+    P.b32 = upload(c, b32.data(), b32.size());
+  }
 }
 
 // factor input: a device pointer to n x ld (padded) data
@@ -455,7 +460,8 @@ hallar_status hallar_eval_A(hallar_t h, const void* U, int32_t r, double* T) {
                                                            (size_t)(m + 1) * sizeof(double));
     if (c->P.C_J != 0.0 || c->P.has_trace) launch_colsum(c, Ud, ld, c->d_colsum, S_PRE);
     // the multipliers do not enter T: b stands in for p with beta = 0
-    launch_grad(c, Ud, ld, r, c->P.b, 0.0, c->d_colsum, GradOut{nullptr, nullptr, Td});
+    const void* bk = c->opt.precision == HALLAR_MIXED ? (const void*)c->P.b32 : (const void*)c->P.b;
+    launch_grad(c, Ud, ld, r, bk, 0.0, c->d_colsum, GradOut{nullptr, nullptr, Td});
     fetch_scalars(c, 0, S_COUNT);
     double* hs = c->h_scal + S_SCALE;
     hs[2] = c->h_scal[S_GRAD] + c->P.C_J * c->h_scal[S_PRE + 1];
@@ -476,22 +482,35 @@ hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
     Ctx* c = h;
     if (!U || !W || !p || r < 1 || r > 256 || !std::isfinite(beta))
       fail(HALLAR_EINVAL, "hallar_grad: bad argument");
+    const bool mixed = c->opt.precision == HALLAR_MIXED;
     const int ld = padded_ld(c, r);
     const int64_t m = c->P.m;
     const void* Ud = stage_factor(c, U, r, ld);
     const double* pd = stage_dvec(c, p, m, &c->stage_m1, &c->stage_m1_bytes);
-    const bool w_direct = is_device_ptr(W) && r == ld && ((uintptr_t)W % 16) == 0;
-    void* Wd = w_direct ? W
-                        : ensure_buffer(c, &c->stage_wout, &c->stage_wout_bytes,
-                                        (size_t)c->P.n * ld * elem_size(c));
-    double* rd = nullptr;
-    if (resid)
+    // the kernel reads p and writes r in the factor type
+    const void* pk = pd;
+    void* rk = nullptr;
+    double* rd = nullptr;  // double residual on the device
+    if (mixed) {
+      void* buf = ensure_buffer(c, &c->stage_pk, &c->stage_pk_bytes, 2 * (size_t)m * sizeof(float));
+      launch_to_factor_type(c, m, buf, pd);
+      pk = buf;
+      if (resid) rk = (float*)buf + m;
+    }
+    if (resid) {
       rd = is_device_ptr(resid) ? resid
                                 : (double*)ensure_buffer(c, (void**)&c->stage_m0,
                                                          &c->stage_m0_bytes,
                                                          (size_t)m * sizeof(double));
+      if (!mixed) rk = rd;
+    }
+    const bool w_direct = is_device_ptr(W) && r == ld && ((uintptr_t)W % 16) == 0;
+    void* Wd = w_direct ? W
+                        : ensure_buffer(c, &c->stage_wout, &c->stage_wout_bytes,
+                                        (size_t)c->P.n * ld * elem_size(c));
     if (c->P.C_J != 0.0 || c->P.has_trace) launch_colsum(c, Ud, ld, c->d_colsum, S_PRE);
-    launch_grad(c, Ud, ld, r, pd, beta, c->d_colsum, GradOut{Wd, rd, nullptr});
+    launch_grad(c, Ud, ld, r, pk, beta, c->d_colsum, GradOut{Wd, rk, nullptr});
+    if (mixed && resid) launch_to_double(c, m, rd, rk);
     fetch_scalars(c, 0, S_COUNT);
     const double* hsc = c->h_scal;
     const double T0 = hsc[S_GRAD] + c->P.C_J * hsc[S_PRE + 1];
@@ -511,12 +530,10 @@ hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
     }
     if (g_val) *g_val = T0 + pr + 0.5 * beta * rr;
     if (!w_direct) {
-      if (r == ld && is_device_ptr(W)) {
+      if (r == ld) {
         HL_CUDA(cudaMemcpyAsync(W, Wd, (size_t)c->P.n * r * elem_size(c),
-                                cudaMemcpyDeviceToDevice, c->stream));
-      } else if (r == ld) {
-        HL_CUDA(cudaMemcpyAsync(W, Wd, (size_t)c->P.n * r * elem_size(c),
-                                cudaMemcpyDeviceToHost, c->stream));
+                                is_device_ptr(W) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
       } else {
         // repack n x ld -> n x r through the stage_u buffer (U is no longer needed)
         void* packed = ensure_buffer(c, &c->stage_u, &c->stage_u_bytes,

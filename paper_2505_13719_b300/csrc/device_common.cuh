@@ -45,6 +45,28 @@ __device__ inline void store_chunk(T* base, int64_t off, const T* o) {
   *reinterpret_cast<VT*>(base + off) = V16<T>::pack(o);
 }
 
+// per-thread accumulation in the factor precision --------------------------
+// double adds directly.  float uses Neumaier's compensated summation (1974):
+// on B300 every double instruction (conversions included) occupies the FP64
+// pipe for many cycles, so the float form keeps its per-row sums in float
+// and carries the rounding error of each addition in a second float; the
+// partial becomes a double only once per thread.
+template <class T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ inline void add(double x) { s += x; }
+  __device__ inline double value() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ inline void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? (s - t) + x : (x - t) + s;
+    s = t;
+  }
+  __device__ inline double value() const { return (double)s + (double)c; }
+};
+
 // sum over the G lanes of a group (G a power of two, groups aligned) -------
 template <int G, class T>
 __device__ inline T group_sum(T v, unsigned mask) {

@@ -41,6 +41,8 @@ struct Problem {
   float* cval32 = nullptr;  // float copy for the mixed form
   double* cdiag = nullptr;  // [n]
   double* b = nullptr;      // [m]
+  float* cdiag32 = nullptr; // float copies for the mixed form
+  float* b32 = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -92,6 +94,7 @@ struct hallar_ctx {
   double* stage_m0 = nullptr; size_t stage_m0_bytes = 0;
   double* stage_m1 = nullptr; size_t stage_m1_bytes = 0;
   double* stage_p0 = nullptr; size_t stage_p0_bytes = 0;
+  void* stage_pk = nullptr; size_t stage_pk_bytes = 0;
   void* eig_stage = nullptr; size_t eig_stage_bytes = 0;
   void* gram_part = nullptr; size_t gram_part_bytes = 0;
   // Lanczos workspace (basis, vectors, partial rows)
@@ -176,8 +179,8 @@ inline int padded_ld(const Ctx* c, int r) {
 // ---------------------------------------------------------------------------
 struct GradOut {
   void* W = nullptr;        // [n x ld] or null
-  double* resid = nullptr;  // [m] or null (owned constraints; the trace row is
-                            // written by the caller)
+  void* resid = nullptr;    // [m] of the factor type, or null (owned constraints;
+                            // the trace row is written by the caller)
   double* T = nullptr;      // [m+1] or null (T[0] and the trace row by the caller)
 };
 
@@ -189,19 +192,20 @@ void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot);
 //   [0] C.UU^T without the C_J part, [1] sum p_l r_l, [2] sum r_l^2 (the
 //   trace row excluded), [3] sum |p'_l| |A_l.UU^T| + |sparse and diagonal
 //   C terms| (the scale of the rounding of g).
-void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double beta,
+// p has the factor's element type (float copy in the mixed form)
+void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
                  const double* colsum, GradOut out);
 // g(Y) - g(X) pieces into S_DIFF: [0] dT0 (no C_J part) [1] p.dT [2] dT(2rX+dT)
 // [3] trace dT = sum <D_i, Y_i + X_i>; rY (if non-null) = rX + dT.
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r,
-                         const double* p, const double* rX, double* rY);
+                         const void* p, const void* rX, void* rY);
 // colsum of D = Y - X and of Y + X (for the C_J part of a value change);
 // S_DIFF[4] = sum <D_i, Y_i + X_i>, S_DIFF[5] = <colsum D, colsum (Y + X)>
 void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD,
                         double* sS);
 
 // r = 1 operator pieces in FP64 (Frank-Wolfe)
-void launch_fw_denom(Ctx* c, const double* y, const double* resid, double tau2, int slot);
+void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, int slot);
 
 // streaming kernels (kernels_vec.cu); reductions into the given slot
 void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst, int r_copy,
@@ -224,6 +228,11 @@ void launch_fw_append(Ctx* c, const void* Y, int ld, int r, const double* y, dou
 // m-length FP64 vectors: op 0: a = b + s cc; op 1: slot = <b, cc>; op 2: slot = |b|^2
 void launch_dvec(Ctx* c, int op, int64_t len, double* a, const double* b, const double* cc,
                  double s, int slot);
+// a = b + s * t with t of the factor type; conversions between double
+// vectors and factor-typed vectors
+void launch_axpy_t(Ctx* c, int64_t len, double* a, const double* b, const void* t, double s);
+void launch_to_factor_type(Ctx* c, int64_t len, void* out, const double* in);
+void launch_to_double(Ctx* c, int64_t len, double* out, const void* in);
 // Gram U^T U (r x r, FP64) and out = U Q (Q row-major r x k)
 void launch_gram(Ctx* c, const void* U, int ld, int r, double* G);
 void launch_right_mult(Ctx* c, const void* U, int ld, int r, const double* Q, int k, void* out,

@@ -27,16 +27,20 @@ struct FamTraits {
   static constexpr bool kCval = FAM != FAM_EDGE;
 };
 
+// Per-row vectors (b, p, the diagonal of C, residuals) have the factor's
+// element type T: the float form reads float copies and keeps every per-row
+// operation in float (see Acc in device_common.cuh); the grid reductions are
+// double.
 struct OpArgs {
   int64_t n;
   int ld;
   const int* __restrict__ rowptr;
   const int* __restrict__ col;
   const int* __restrict__ code;
-  const void* __restrict__ cval;      // element type of the factor
-  const double* __restrict__ cdiag;
-  const double* __restrict__ b;
-  const double* __restrict__ p;
+  const void* __restrict__ cval;      // T
+  const void* __restrict__ cdiag;     // T
+  const void* __restrict__ b;         // T
+  const void* __restrict__ p;         // T
   double C_J;
   double beta;
   int has_trace;
@@ -53,8 +57,8 @@ struct GradIO {
   const void* __restrict__ U;
   const double* __restrict__ colsum;  // [ld] or null: C_J 11^T U = 1 (colsum)^T
   const double* __restrict__ pre;     // pre[0] = |U|_F^2 (trace row)
-  void* __restrict__ W;               // or null
-  double* __restrict__ resid;         // or null
+  void* __restrict__ W;               // T, or null
+  void* __restrict__ resid;           // T, or null
   double* __restrict__ Tout;          // T[1 + l] or null
 };
 
@@ -64,17 +68,22 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
   constexpr int VEC = V16<T>::N;
   const T* __restrict__ U = static_cast<const T*>(io.U);
   const T* __restrict__ cval = static_cast<const T*>(a.cval);
+  const T* __restrict__ cdiag = static_cast<const T*>(a.cdiag);
+  const T* __restrict__ bv = static_cast<const T*>(a.b);
+  const T* __restrict__ pv = static_cast<const T*>(a.p);
   T* __restrict__ W = static_cast<T*>(io.W);
+  T* __restrict__ resid = static_cast<T*>(io.resid);
   const int lane_g = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
   const int nch = a.ld / VEC;
+  const T beta = (T)a.beta;
 
   // shifted multiplier of the trace row, identical for every row
-  double ps_tr = 0.0;
+  T ps_tr = (T)0;
   if (Tr::kPairs && a.has_trace) {
-    const double rt = io.pre[0] - a.b[a.trace_row];
-    ps_tr = a.p[a.trace_row] + a.beta * rt;
+    const double rt = io.pre[0] - (double)bv[a.trace_row];
+    ps_tr = (T)((double)pv[a.trace_row] + a.beta * rt);
   }
   // the C_J 11^T U term adds C_J * colsum to every row of W
   T cj[K][VEC];
@@ -88,7 +97,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
 
   // C.UU^T (sparse + diagonal part), p.r, r.r, and the magnitude
   // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  Acc<T> acc_t0, acc_pr, acc_rr, acc_mag;
   for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
     T u[K][VEC], acc[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
@@ -111,17 +120,19 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       for (int v = 0; v < VEC; ++v) nrm_l = fma(u[k][v], u[k][v], nrm_l);
     const T nrm = group_sum<G>(nrm_l, gmask);  // |U_i|^2
 
-    double dcoef = a.cdiag[i];
+    const T cdi = cdiag[i];
+    T dcoef = cdi;
     if (Tr::kDiag) {
       // constraint i: A_i . UU^T = |U_i|^2
-      const double r = (double)nrm - a.b[i];
-      const double pi = a.p[i];
-      dcoef += pi + a.beta * r;
+      const T r = nrm - bv[i];
+      const T pi = pv[i];
+      const T ps = fma(beta, r, pi);
+      dcoef += ps;
       if (lane_g == 0) {
-        red[1] += pi * r;
-        red[2] += r * r;
-        red[3] += fabs(pi + a.beta * r) * (double)nrm;
-        if (io.resid) io.resid[i] = r;
+        acc_pr.add(pi * r);
+        acc_rr.add(r * r);
+        acc_mag.add(fabs(ps) * nrm);
+        if (resid) resid[i] = r;
         if (io.Tout) io.Tout[i] = (double)nrm;
       }
     }
@@ -163,14 +174,15 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
           const T dot = group_sum<G>(d_l, gmask);
           const bool owner = cd >= 0;
           const int l = owner ? cd : -cd - 1;
-          const double r = (double)dot - a.b[l];
-          const double pl = a.p[l];
-          coef = (T)(0.5 * (pl + a.beta * r));
+          const T r = dot - bv[l];
+          const T pl = pv[l];
+          const T ps = fma(beta, r, pl);
+          coef = (T)0.5 * ps;
           if (owner && lane_g == 0) {
-            red[1] += pl * r;
-            red[2] += r * r;
-            red[3] += fabs(pl + a.beta * r) * fabs((double)dot);
-            if (io.resid) io.resid[l] = r;
+            acc_pr.add(pl * r);
+            acc_rr.add(r * r);
+            acc_mag.add(fabs(ps) * fabs(dot));
+            if (resid) resid[l] = r;
             if (io.Tout) io.Tout[l] = (double)dot;
           }
         }
@@ -183,27 +195,27 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
           acc[k][v] = fma(coef, uj[k][v], acc[k][v]);
         }
     }
-    red[0] += (double)cdot_l;
-    red[3] += fabs((double)cdot_l);
+    acc_t0.add(cdot_l);
+    acc_mag.add(fabs(cdot_l));
     if (lane_g == 0) {
-      red[0] += a.cdiag[i] * (double)nrm;
-      red[3] += fabs(a.cdiag[i]) * (double)nrm;
+      acc_t0.add(cdi * nrm);
+      acc_mag.add(fabs(cdi) * nrm);
     }
 
     if (W != nullptr) {
-      const T dc = (T)dcoef;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int ch = lane_g + k * G;
         if (ch < nch) {
           T w[VEC];
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) w[v] = fma(dc, u[k][v], acc[k][v]) + cj[k][v];
+          for (int v = 0; v < VEC; ++v) w[v] = fma(dcoef, u[k][v], acc[k][v]) + cj[k][v];
           store_chunk<T>(W, rowoff + ch * VEC, w);
         }
       }
     }
   }
+  double red[4] = {acc_t0.value(), acc_pr.value(), acc_rr.value(), acc_mag.value()};
   grid_reduce<4>(red, a.partials, a.counter, a.out);
 }
 
@@ -214,8 +226,8 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
 struct DiffIO {
   const void* __restrict__ X;
   const void* __restrict__ Y;
-  const double* __restrict__ rX;
-  double* __restrict__ rY;  // or null
+  const void* __restrict__ rX;  // T
+  void* __restrict__ rY;        // T, or null
 };
 
 template <class T, int FAM, int G, int K>
@@ -224,14 +236,18 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
   constexpr int VEC = V16<T>::N;
   const T* __restrict__ X = static_cast<const T*>(io.X);
   const T* __restrict__ Y = static_cast<const T*>(io.Y);
+  const T* __restrict__ rXv = static_cast<const T*>(io.rX);
+  T* __restrict__ rYv = static_cast<T*>(io.rY);
   const T* __restrict__ cval = static_cast<const T*>(a.cval);
+  const T* __restrict__ cdiag = static_cast<const T*>(a.cdiag);
+  const T* __restrict__ pv = static_cast<const T*>(a.p);
   const int lane_g = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
   const int nch = a.ld / VEC;
 
   // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT
-  double red[4] = {0.0, 0.0, 0.0, 0.0};
+  Acc<T> acc_t0, acc_pd, acc_q, acc_tr;
   for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
     T x[K][VEC], d[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
@@ -255,15 +271,15 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
     for (int k = 0; k < K; ++k)
 #pragma unroll
       for (int v = 0; v < VEC; ++v) own_l = fma(d[k][v], d[k][v] + (T)2 * x[k][v], own_l);
-    red[3] += (double)own_l;               // trace row change (lane parts)
-    red[0] += a.cdiag[i] * (double)own_l;  // diagonal of C
+    acc_tr.add(own_l);               // trace row change (lane parts)
+    acc_t0.add(cdiag[i] * own_l);    // diagonal of C
     if (Tr::kDiag) {
-      const T dTi = group_sum<G>(own_l, gmask);
+      const T dt = group_sum<G>(own_l, gmask);
       if (lane_g == 0) {
-        const double dt = (double)dTi, rx = io.rX[i];
-        red[1] += a.p[i] * dt;
-        red[2] += dt * (2.0 * rx + dt);
-        if (io.rY) io.rY[i] = rx + dt;
+        const T rx = rXv[i];
+        acc_pd.add(pv[i] * dt);
+        acc_q.add(dt * ((T)2 * rx + dt));
+        if (rYv) rYv[i] = rx + dt;
       }
     }
     const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
@@ -296,17 +312,18 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
         cd_l = fma(cval[e], pd, cd_l);
       } else {
         // owned pair constraint l: dT_l = <Y_i,Y_j> - <X_i,X_j>
-        const T dTl = group_sum<G>(pd, gmask);
+        const T dt = group_sum<G>(pd, gmask);
         if (lane_g == 0) {
-          const double dt = (double)dTl, rx = io.rX[cd];
-          red[1] += a.p[cd] * dt;
-          red[2] += dt * (2.0 * rx + dt);
-          if (io.rY) io.rY[cd] = rx + dt;
+          const T rx = rXv[cd];
+          acc_pd.add(pv[cd] * dt);
+          acc_q.add(dt * ((T)2 * rx + dt));
+          if (rYv) rYv[cd] = rx + dt;
         }
       }
     }
-    red[0] += (double)cd_l;
+    acc_t0.add(cd_l);
   }
+  double red[4] = {acc_t0.value(), acc_pd.value(), acc_q.value(), acc_tr.value()};
   grid_reduce<4>(red, a.partials, a.counter, a.out);
 }
 
@@ -332,28 +349,26 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
   const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
   const int c = threadIdx.x % ld;
   const int rsub = threadIdx.x / ld;
-  double acc = 0.0, acc2 = 0.0, nrm = 0.0;
+  Acc<T> acc, acc2, nrm;
   if (rsub < rows_per_pass) {
     for (int64_t i = (int64_t)blockIdx.x * rows_per_pass + rsub; i < n;
          i += (int64_t)gridDim.x * rows_per_pass) {
-      const T xv = U[i * ld + c];
-      const double x = (double)xv;
+      const T x = U[i * ld + c];
       if (mode == 0) {
-        acc += x;
-        nrm += x * x;
+        acc.add(x);
+        nrm.add(x * x);
       } else {
-        const T yv = Y[i * ld + c];
-        const double y = (double)yv;
-        const double dd = (double)(yv - xv);
-        acc += dd;
-        acc2 += y + x;
-        nrm += dd * (y + x);
+        const T y = Y[i * ld + c];
+        const T dd = y - x;
+        acc.add(dd);
+        acc2.add(y + x);
+        nrm.add(dd * (y + x));
       }
     }
   }
-  t1[threadIdx.x] = acc;
-  t2[threadIdx.x] = acc2;
-  double red[1] = {nrm};
+  t1[threadIdx.x] = acc.value();
+  t2[threadIdx.x] = acc2.value();
+  double red[1] = {nrm.value()};
   block_sum<1>(red, shr);  // contains __syncthreads
   const int W = ld + 1;
   for (int cc = threadIdx.x; cc < ld; cc += kBlock) {
@@ -401,12 +416,13 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
 
 // ---------------------------------------------------------------------------
 // Frank-Wolfe denominator sum_l (A_l.YY^T - tau^2 A_l.yy^T)^2 over the
-// non-trace constraints, with A_l.YY^T = r_l + b_l (FP64, r = 1 gathers)
+// non-trace constraints, with A_l.YY^T = r_l + b_l (r = 1 gathers, FP64; run
+// once per Frank-Wolfe step)
 // ---------------------------------------------------------------------------
-template <int FAM>
-__global__ void __launch_bounds__(kBlock) k_fw_denom(OpArgs a, const double* __restrict__ y,
-                                                     const double* __restrict__ resid,
-                                                     double tau2) {
+template <class T, int FAM>
+__global__ void __launch_bounds__(kBlock) k_fw_denom(OpArgs a, const double* __restrict__ bd,
+                                                     const double* __restrict__ y,
+                                                     const T* __restrict__ resid, double tau2) {
   using Tr = FamTraits<FAM>;
   double red[2] = {0.0, 0.0};  // sum of squares, |y|^2
   for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n;
@@ -414,14 +430,14 @@ __global__ void __launch_bounds__(kBlock) k_fw_denom(OpArgs a, const double* __r
     const double yi = y[i];
     red[1] += yi * yi;
     if (Tr::kDiag) {
-      const double dl = resid[i] + a.b[i] - tau2 * yi * yi;
+      const double dl = (double)resid[i] + bd[i] - tau2 * yi * yi;
       red[0] += dl * dl;
     } else {
       const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
       for (int e = e0; e < e1; ++e) {
         const int cd = a.code[e];
         if (cd < 0) continue;  // mirrored or pure C entry
-        const double dl = resid[cd] + a.b[cd] - tau2 * yi * __ldcg(&y[a.col[e]]);
+        const double dl = (double)resid[cd] + bd[cd] - tau2 * yi * __ldcg(&y[a.col[e]]);
         red[0] += dl * dl;
       }
     }
@@ -440,9 +456,10 @@ OpArgs make_args(Ctx* c, int ld, int slot) {
   a.rowptr = P.rowptr;
   a.col = P.col;
   a.code = P.code;
-  a.cval = c->opt.precision == HALLAR_MIXED ? (const void*)P.cval32 : (const void*)P.cval;
-  a.cdiag = P.cdiag;
-  a.b = P.b;
+  const bool mixed = c->opt.precision == HALLAR_MIXED;
+  a.cval = mixed ? (const void*)P.cval32 : (const void*)P.cval;
+  a.cdiag = mixed ? (const void*)P.cdiag32 : (const void*)P.cdiag;
+  a.b = mixed ? (const void*)P.b32 : (const void*)P.b;
   a.p = nullptr;
   a.C_J = P.C_J;
   a.beta = 0.0;
@@ -520,7 +537,7 @@ double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool rea
   return b;
 }
 
-void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double beta,
+void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
                  const double* colsum, GradOut out) {
   (void)r;
   if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
@@ -543,8 +560,8 @@ void launch_grad(Ctx* c, const void* U, int ld, int r, const double* p, double b
   prof_end(c, tok);
 }
 
-void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const double* p,
-                         const double* rX, double* rY) {
+void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const void* p,
+                         const void* rX, void* rY) {
   (void)r;
   OpArgs a = make_args(c, ld, S_DIFF);
   a.p = p;
@@ -589,14 +606,23 @@ void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD
   HL_CHECK_LAUNCH(c);
 }
 
-void launch_fw_denom(Ctx* c, const double* y, const double* resid, double tau2, int slot) {
+void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, int slot) {
   OpArgs a = make_args(c, 1, slot);
   const int grid = grid_for(c, c->P.n, kBlock);
+  const bool mixed = c->opt.precision == HALLAR_MIXED;
+#define HL_FWD(FAMV)                                                                          \
+  if (mixed)                                                                                  \
+    k_fw_denom<float, FAMV><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y, (const float*)resid, \
+                                                            tau2);                            \
+  else                                                                                        \
+    k_fw_denom<double, FAMV><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y,                   \
+                                                             (const double*)resid, tau2)
   switch (c->P.fam) {
-    case FAM_DIAG: k_fw_denom<FAM_DIAG><<<grid, kBlock, 0, c->stream>>>(a, y, resid, tau2); break;
-    case FAM_EDGE: k_fw_denom<FAM_EDGE><<<grid, kBlock, 0, c->stream>>>(a, y, resid, tau2); break;
-    default: k_fw_denom<FAM_EDGE_C><<<grid, kBlock, 0, c->stream>>>(a, y, resid, tau2); break;
+    case FAM_DIAG: HL_FWD(FAM_DIAG); break;
+    case FAM_EDGE: HL_FWD(FAM_EDGE); break;
+    default: HL_FWD(FAM_EDGE_C); break;
   }
+#undef HL_FWD
   HL_CHECK_LAUNCH(c);
 }
 

@@ -14,13 +14,18 @@ namespace {
 template <class T, int NS, class Op>
 __global__ void __launch_bounds__(kBlock) k_stream(int64_t nvec, Op op, double* partials,
                                                    unsigned* counter, double* out) {
-  double red[NS > 0 ? NS : 1];
-#pragma unroll
-  for (int s = 0; s < (NS > 0 ? NS : 1); ++s) red[s] = 0.0;
+  Acc<T> red[NS > 0 ? NS : 1];
+  Op o = op;
+  o.setup();  // per-thread constants, computed once
   for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < nvec;
        v += (int64_t)gridDim.x * kBlock)
-    op(v, red);
-  if constexpr (NS > 0) grid_reduce<NS>(red, partials, counter, out);
+    o(v, red);
+  if constexpr (NS > 0) {
+    double r[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) r[s] = red[s].value();
+    grid_reduce<NS>(r, partials, counter, out);
+  }
 }
 
 template <class T, int NS, class Op>
@@ -35,34 +40,40 @@ void run_stream(Ctx* c, int64_t nelem, const Op& op, int slot) {
 
 #define HL_LOAD(ptr, v, arr) load_chunk<T>((ptr), (v) * VEC, arr)
 
+// every element operation runs in the factor type T (float in the mixed
+// form: double instructions are the scarce resource on B300); reductions
+// accumulate in Acc<T>
+struct OpBase {
+  __device__ void setup() {}
+};
+
 // xt = (A y + a x) / (A + a)      (ADAP-FISTA step 2)
 template <class T>
-struct OpXt {
-  T* xt; const T* y; const T* x; double wy, wx;
-  __device__ void operator()(int64_t v, double*) const {
+struct OpXt : OpBase {
+  T* xt; const T* y; const T* x; T wy, wx;
+  __device__ void operator()(int64_t v, Acc<T>*) const {
     constexpr int VEC = V16<T>::N;
     T a[VEC], b[VEC], o[VEC];
     HL_LOAD(y, v, a);
     HL_LOAD(x, v, b);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) o[k] = (T)(wy * (double)a[k] + wx * (double)b[k]);
+    for (int k = 0; k < VEC; ++k) o[k] = fma(wy, a[k], wx * b[k]);
     store_chunk<T>(xt, v * VEC, o);
   }
 };
 
 // x <- (mu a y + tk x - a s) / tk_new, s = (L - mu)(xt - y)   (step 3)
 template <class T>
-struct OpX {
-  T* x; const T* y; const T* xt; double cy, cx, cxt;
-  __device__ void operator()(int64_t v, double*) const {
+struct OpX : OpBase {
+  T* x; const T* y; const T* xt; T cy, cx, cxt;
+  __device__ void operator()(int64_t v, Acc<T>*) const {
     constexpr int VEC = V16<T>::N;
     T a[VEC], b[VEC], t[VEC], o[VEC];
     HL_LOAD(y, v, a);
     HL_LOAD(x, v, b);
     HL_LOAD(xt, v, t);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k)
-      o[k] = (T)(cy * (double)a[k] + cx * (double)b[k] + cxt * (double)t[k]);
+    for (int k = 0; k < VEC; ++k) o[k] = fma(cy, a[k], fma(cx, b[k], cxt * t[k]));
     store_chunk<T>(x, v * VEC, o);
   }
 };
@@ -70,20 +81,22 @@ struct OpX {
 // z = xt - grad psi_s(xt) / L with grad psi_s = 2 lam W + xt - center;
 // red[0] = |z|^2 (the ball projection is the scaling min(1, tau/|z|))
 template <class T>
-struct OpZ {
-  T* z; const T* xt; const T* W; const T* ctr; double c2lam, invL;
-  __device__ void operator()(int64_t v, double* red) const {
+struct OpZ : OpBase {
+  T* z; const T* xt; const T* W; const T* ctr; T c2lam, invL;
+  __device__ void operator()(int64_t v, Acc<T>* red) const {
     constexpr int VEC = V16<T>::N;
     T a[VEC], w[VEC], cc[VEC], o[VEC];
     HL_LOAD(xt, v, a);
     HL_LOAD(W, v, w);
     HL_LOAD(ctr, v, cc);
+    T s = (T)0;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-      const double g = c2lam * (double)w[k] + ((double)a[k] - (double)cc[k]);
-      o[k] = (T)((double)a[k] - invL * g);
-      red[0] += (double)o[k] * (double)o[k];
+      const T g = fma(c2lam, w[k], a[k] - cc[k]);
+      o[k] = fma(-invL, g, a[k]);
+      s = fma(o[k], o[k], s);
     }
+    red[0].add(s);
     store_chunk<T>(z, v * VEC, o);
   }
 };
@@ -93,27 +106,36 @@ struct OpZ {
 // red = [|d|^2, <g, d>, <d, (y + xt)/2 - center>, |y - center|^2]
 template <class T>
 struct OpY {
-  T* y; const T* z; const T* xt; const T* ctr; const T* W; const double* z2; double tau, c2lam;
-  __device__ void operator()(int64_t v, double* red) const {
-    constexpr int VEC = V16<T>::N;
+  T* y; const T* z; const T* xt; const T* ctr; const T* W; const double* z2; double tau;
+  T c2lam;
+  T cs;
+  __device__ void setup() {
     const double zn = sqrt(*z2);
-    const double cs = zn > tau ? tau / zn : 1.0;
+    cs = (T)(zn > tau ? tau / zn : 1.0);
+  }
+  __device__ void operator()(int64_t v, Acc<T>* red) const {
+    constexpr int VEC = V16<T>::N;
     T zz[VEC], a[VEC], cc[VEC], w[VEC], o[VEC];
     HL_LOAD(z, v, zz);
     HL_LOAD(xt, v, a);
     HL_LOAD(ctr, v, cc);
     HL_LOAD(W, v, w);
+    T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-      o[k] = (T)(cs * (double)zz[k]);
-      const double yk = (double)o[k], xk = (double)a[k], ck = (double)cc[k];
-      const double d = yk - xk;
-      const double g = c2lam * (double)w[k] + (xk - ck);
-      red[0] += d * d;
-      red[1] += g * d;
-      red[2] += d * (0.5 * (yk + xk) - ck);
-      red[3] += (yk - ck) * (yk - ck);
+      o[k] = cs * zz[k];
+      const T d = o[k] - a[k];
+      const T g = fma(c2lam, w[k], a[k] - cc[k]);
+      const T yc = o[k] - cc[k];
+      s0 = fma(d, d, s0);
+      s1 = fma(g, d, s1);
+      s2 = fma(d, (T)0.5 * (o[k] + a[k]) - cc[k], s2);
+      s3 = fma(yc, yc, s3);
     }
+    red[0].add(s0);
+    red[1].add(s1);
+    red[2].add(s2);
+    red[3].add(s3);
     store_chunk<T>(y, v * VEC, o);
   }
 };
@@ -122,75 +144,82 @@ struct OpY {
 // V = 2 lam W(y) + (y - center) + L (z - y), D = y - center:
 // red = [<V, D>, |D|^2, |V - D|^2]   (R_j = (V - D) / lam, eq. Rj def)
 template <class T>
-struct OpAipp {
-  const T* Wy; const T* z; const T* y; const T* ctr; double c2lam, L;
-  __device__ void operator()(int64_t v, double* red) const {
+struct OpAipp : OpBase {
+  const T* Wy; const T* z; const T* y; const T* ctr; T c2lam, L;
+  __device__ void operator()(int64_t v, Acc<T>* red) const {
     constexpr int VEC = V16<T>::N;
     T w[VEC], zz[VEC], yy[VEC], cc[VEC];
     HL_LOAD(Wy, v, w);
     HL_LOAD(z, v, zz);
     HL_LOAD(y, v, yy);
     HL_LOAD(ctr, v, cc);
+    T s0 = (T)0, s1 = (T)0, s2 = (T)0;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-      const double D = (double)yy[k] - (double)cc[k];
-      const double VmD = c2lam * (double)w[k] + L * ((double)zz[k] - (double)yy[k]);
-      const double V = VmD + D;
-      red[0] += V * D;
-      red[1] += D * D;
-      red[2] += VmD * VmD;
+      const T D = yy[k] - cc[k];
+      const T VmD = fma(c2lam, w[k], L * (zz[k] - yy[k]));
+      s0 = fma(VmD + D, D, s0);
+      s1 = fma(D, D, s1);
+      s2 = fma(VmD, VmD, s2);
     }
+    red[0].add(s0);
+    red[1].add(s1);
+    red[2].add(s2);
   }
 };
 
 template <class T>
-struct OpScale {
-  T* u; double s;
-  __device__ void operator()(int64_t v, double*) const {
+struct OpScale : OpBase {
+  T* u; T s;
+  __device__ void operator()(int64_t v, Acc<T>*) const {
     constexpr int VEC = V16<T>::N;
     T a[VEC];
     HL_LOAD(u, v, a);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) a[k] = (T)(s * (double)a[k]);
+    for (int k = 0; k < VEC; ++k) a[k] = s * a[k];
     store_chunk<T>(u, v * VEC, a);
   }
 };
 
 template <class T>
-struct OpNorm2 {
+struct OpNorm2 : OpBase {
   const T* u;
-  __device__ void operator()(int64_t v, double* red) const {
+  __device__ void operator()(int64_t v, Acc<T>* red) const {
     constexpr int VEC = V16<T>::N;
     T a[VEC];
     HL_LOAD(u, v, a);
+    T s = (T)0;
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) red[0] += (double)a[k] * (double)a[k];
+    for (int k = 0; k < VEC; ++k) s = fma(a[k], a[k], s);
+    red[0].add(s);
   }
 };
 
 template <class T>
-struct OpDot {
+struct OpDot : OpBase {
   const T* a; const T* b;
-  __device__ void operator()(int64_t v, double* red) const {
+  __device__ void operator()(int64_t v, Acc<T>* red) const {
     constexpr int VEC = V16<T>::N;
     T x[VEC], y[VEC];
     HL_LOAD(a, v, x);
     HL_LOAD(b, v, y);
+    T s = (T)0;
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) red[0] += (double)x[k] * (double)y[k];
+    for (int k = 0; k < VEC; ++k) s = fma(x[k], y[k], s);
+    red[0].add(s);
   }
 };
 
 // padded, scaled row copy: dst[i, 0:r_copy] = s * src[i, 0:r_copy], rest 0
 template <class T>
 __global__ void k_pad_copy(const T* __restrict__ src, int ld_src, T* __restrict__ dst, int ld_dst,
-                           int r_copy, int64_t n, double s) {
+                           int r_copy, int64_t n, T s) {
   const int64_t total = n * ld_dst;
   for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * kBlock) {
     const int64_t i = e / ld_dst;
     const int c = (int)(e - i * ld_dst);
-    dst[e] = c < r_copy ? (T)(s * (double)src[i * ld_src + c]) : (T)0;
+    dst[e] = c < r_copy ? s * src[i * ld_src + c] : (T)0;
   }
 }
 
@@ -198,17 +227,17 @@ __global__ void k_pad_copy(const T* __restrict__ src, int ld_src, T* __restrict_
 // Ynew[i, r] = sy y_i when appending, zero padding
 template <class T>
 __global__ void k_fw_append(const T* __restrict__ Y, int ld, int r, const double* __restrict__ y,
-                            double sY, double sy, T* __restrict__ Yn, int ld_new, int append,
+                            T sY, double sy, T* __restrict__ Yn, int ld_new, int append,
                             int64_t n) {
   const int64_t total = n * ld_new;
   for (int64_t e = (int64_t)blockIdx.x * kBlock + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * kBlock) {
     const int64_t i = e / ld_new;
     const int c = (int)(e - i * ld_new);
-    double val = 0.0;
-    if (c < r) val = sY * (double)Y[i * ld + c];
-    else if (append && c == r) val = sy * y[i];
-    Yn[e] = (T)val;
+    T val = (T)0;
+    if (c < r) val = sY * Y[i * ld + c];
+    else if (append && c == r) val = (T)(sy * y[i]);
+    Yn[e] = val;
   }
 }
 
@@ -229,6 +258,23 @@ __global__ void __launch_bounds__(kBlock) k_dvec(int64_t len, OpDvec op, double*
        i += (int64_t)gridDim.x * kBlock)
     op(i, red);
   grid_reduce<1>(red, partials, counter, out);
+}
+
+// a = b + s * (double) t, t of the factor type (dual update, p' for Lanczos)
+template <class T>
+__global__ void k_axpy_t(int64_t len, double* __restrict__ a, const double* __restrict__ b,
+                         const T* __restrict__ t, double s) {
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * kBlock)
+    a[i] = b[i] + s * (double)t[i];
+}
+
+// out = (To) in, elementwise
+template <class To, class Ti>
+__global__ void k_convert(int64_t len, To* __restrict__ out, const Ti* __restrict__ in) {
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * kBlock)
+    out[i] = (To)in[i];
 }
 
 // Gram U^T U (rank trim): block b accumulates rows b*8.., stepping by the
@@ -310,7 +356,8 @@ __global__ void k_right_mult(const T* __restrict__ U, int ld, int r, const doubl
 void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, double a, int ld) {
   const int64_t ne = c->P.n * (int64_t)ld;
   const double wy = A / (A + a), wx = a / (A + a);
-  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXt<T>{(T*)xt, (const T*)y, (const T*)x, wy, wx}, -1));
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXt<T>{{}, (T*)xt, (const T*)y, (const T*)x, (T)wy, (T)wx},
+                                 -1));
 }
 
 void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, double a,
@@ -320,15 +367,16 @@ void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, d
   const double cy = (mu * a + a * (L - mu)) / tk_new;
   const double cx = tk / tk_new;
   const double cxt = -a * (L - mu) / tk_new;
-  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpX<T>{(T*)x, (const T*)y, (const T*)xt, cy, cx, cxt}, -1));
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpX<T>{{}, (T*)x, (const T*)y, (const T*)xt, (T)cy, (T)cx,
+                                               (T)cxt}, -1));
 }
 
 void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,
                     double lam, double L, int ld) {
   const int64_t ne = c->P.n * (int64_t)ld;
   const double c2lam = 2.0 * lam, invL = 1.0 / L;
-  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpZ<T>{(T*)z, (const T*)xt, (const T*)W, (const T*)center,
-                                               c2lam, invL}, S_SCALE));
+  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpZ<T>{{}, (T*)z, (const T*)xt, (const T*)W,
+                                               (const T*)center, (T)c2lam, (T)invL}, S_SCALE));
 }
 
 void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* center,
@@ -337,30 +385,48 @@ void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* 
   const double* z2 = c->d_scal + S_SCALE;
   const double c2lam = 2.0 * lam;
   HL_BY_TYPE(c, run_stream<T, 4>(c, ne, OpY<T>{(T*)y, (const T*)z, (const T*)xt, (const T*)center,
-                                               (const T*)W, z2, tau, c2lam}, S_VEC));
+                                               (const T*)W, z2, tau, (T)c2lam, (T)0}, S_VEC));
 }
 
 void launch_aipp_check(Ctx* c, const void* Wy, const void* z, const void* y, const void* center,
                        double lam, double L, int ld) {
   const int64_t ne = c->P.n * (int64_t)ld;
   const double c2lam = 2.0 * lam;
-  HL_BY_TYPE(c, run_stream<T, 3>(c, ne, OpAipp<T>{(const T*)Wy, (const T*)z, (const T*)y,
-                                                  (const T*)center, c2lam, L}, S_VEC2));
+  HL_BY_TYPE(c, run_stream<T, 3>(c, ne, OpAipp<T>{{}, (const T*)Wy, (const T*)z, (const T*)y,
+                                                  (const T*)center, (T)c2lam, (T)L}, S_VEC2));
 }
 
 void launch_scale(Ctx* c, void* U, int ld, double s) {
   const int64_t ne = c->P.n * (int64_t)ld;
-  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpScale<T>{(T*)U, s}, -1));
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpScale<T>{{}, (T*)U, (T)s}, -1));
 }
 
 void launch_norm2(Ctx* c, const void* U, int ld, int slot) {
   const int64_t ne = c->P.n * (int64_t)ld;
-  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpNorm2<T>{(const T*)U}, slot));
+  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpNorm2<T>{{}, (const T*)U}, slot));
 }
 
 void launch_dot(Ctx* c, const void* W, const void* U, int ld, int slot) {
   const int64_t ne = c->P.n * (int64_t)ld;
-  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpDot<T>{(const T*)W, (const T*)U}, slot));
+  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpDot<T>{{}, (const T*)W, (const T*)U}, slot));
+}
+
+void launch_axpy_t(Ctx* c, int64_t len, double* a, const double* b, const void* t, double s) {
+  const int grid = grid_for(c, len, kBlock * 4);
+  HL_BY_TYPE(c, k_axpy_t<T><<<grid, kBlock, 0, c->stream>>>(len, a, b, (const T*)t, s));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_to_factor_type(Ctx* c, int64_t len, void* out, const double* in) {
+  const int grid = grid_for(c, len, kBlock * 4);
+  HL_BY_TYPE(c, k_convert<T, double><<<grid, kBlock, 0, c->stream>>>(len, (T*)out, in));
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_to_double(Ctx* c, int64_t len, double* out, const void* in) {
+  const int grid = grid_for(c, len, kBlock * 4);
+  HL_BY_TYPE(c, k_convert<double, T><<<grid, kBlock, 0, c->stream>>>(len, out, (const T*)in));
+  HL_CHECK_LAUNCH(c);
 }
 
 void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst, int r_copy,
@@ -368,7 +434,8 @@ void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst,
   const int64_t total = c->P.n * (int64_t)ld_dst;
   const int grid = grid_for(c, total, kBlock * 4);
   HL_BY_TYPE(c, k_pad_copy<T><<<grid, kBlock, 0, c->stream>>>((const T*)src, ld_src, (T*)dst,
-                                                             ld_dst, r_copy, c->P.n, scale_src));
+                                                             ld_dst, r_copy, c->P.n,
+                                                             (T)scale_src));
   HL_CHECK_LAUNCH(c);
 }
 
@@ -376,7 +443,7 @@ void launch_fw_append(Ctx* c, const void* Y, int ld, int r, const double* y, dou
                       void* Ynew, int ld_new, int append) {
   const int64_t total = c->P.n * (int64_t)ld_new;
   const int grid = grid_for(c, total, kBlock * 4);
-  HL_BY_TYPE(c, k_fw_append<T><<<grid, kBlock, 0, c->stream>>>((const T*)Y, ld, r, y, sY, sy,
+  HL_BY_TYPE(c, k_fw_append<T><<<grid, kBlock, 0, c->stream>>>((const T*)Y, ld, r, y, (T)sY, sy,
                                                               (T*)Ynew, ld_new, append, c->P.n));
   HL_CHECK_LAUNCH(c);
 }

@@ -34,8 +34,11 @@ namespace hallar {
 
 namespace {
 
-__global__ void k_trace_fix(double* dst, const double* src, const double* dscal, double add) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) dst[0] = (src ? src[0] : 0.0) + dscal[0] + add;
+// trace-row residual (factor type) from a device scalar: dst = src + dscal + add
+template <class T>
+__global__ void k_trace_fix(T* dst, const T* src, const double* dscal, double add) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    dst[0] = (T)((src ? (double)src[0] : 0.0) + dscal[0] + add);
 }
 
 // symmetric r x r eigendecomposition by cyclic Jacobi rotations (rank trim)
@@ -93,7 +96,11 @@ struct Solver {
   size_t fbytes = 0;  // bytes of one factor buffer
   void *Ytil = nullptr, *ctr = nullptr, *x = nullptr, *y = nullptr, *xt = nullptr, *z = nullptr;
   void *ynew = nullptr, *Wg = nullptr, *Wy = nullptr, *tmp = nullptr;
-  double *p = nullptr, *r_ctr = nullptr, *rX = nullptr, *rY = nullptr, *pshift = nullptr;
+  // p: the multipliers (double, the dual update's precision); pk: the copy of
+  // the factor type that the operator kernels read (p itself in FP64);
+  // residual vectors have the factor type
+  double *p = nullptr, *pshift = nullptr;
+  void *pk = nullptr, *r_ctr = nullptr, *rX = nullptr, *rY = nullptr;
   double *v = nullptr, *vprev = nullptr, *v0 = nullptr, *gram = nullptr;
   int rank = 0, ld = 0;
   double beta = 1.0, lam = 1.0, Mbar = 1.0, p_tr = 0.0, b_tr = 0.0;
@@ -126,9 +133,10 @@ struct Solver {
     Ytil = fbuf(); ctr = fbuf(); x = fbuf(); y = fbuf(); xt = fbuf(); z = fbuf();
     ynew = fbuf(); Wg = fbuf(); Wy = fbuf(); tmp = fbuf();
     p = salloc<double>(m);
-    r_ctr = salloc<double>(m);
-    rX = salloc<double>(m);
-    rY = salloc<double>(m);
+    pk = o.precision == HALLAR_MIXED ? (void*)salloc<float>(m) : (void*)p;
+    r_ctr = salloc<unsigned char>(m * elem_size(c));
+    rX = salloc<unsigned char>(m * elem_size(c));
+    rY = salloc<unsigned char>(m * elem_size(c));
     pshift = salloc<double>(m);
     v = salloc<double>(n);
     vprev = salloc<double>(n);
@@ -142,14 +150,28 @@ struct Solver {
                             c->stream));
   }
 
+  // trace-row entry of a residual vector from a device scalar
+  void trace_fix(void* r, const void* src, const double* dscal, double add) {
+    if (o.precision == HALLAR_MIXED)
+      k_trace_fix<float><<<1, 32, 0, c->stream>>>((float*)r + (m - 1),
+                                                   src ? (const float*)src + (m - 1) : nullptr,
+                                                   dscal, add);
+    else
+      k_trace_fix<double><<<1, 32, 0, c->stream>>>((double*)r + (m - 1),
+                                                    src ? (const double*)src + (m - 1) : nullptr,
+                                                    dscal, add);
+    HL_CHECK_LAUNCH(c);
+  }
+  // the kernels' copy of p after p changed
+  void refresh_pk() {
+    if (pk != (void*)p) launch_to_factor_type(c, m, pk, p);
+  }
+
   // enqueue: pre-pass + fused operator at U (W and resid optional)
-  void grad_enqueue(const void* U, void* W, double* resid) {
+  void grad_enqueue(const void* U, void* W, void* resid) {
     if (P.C_J != 0.0 || P.has_trace) launch_colsum(c, U, ld, c->d_colsum, S_PRE);
-    launch_grad(c, U, ld, rank, p, beta, c->d_colsum, GradOut{W, resid, nullptr});
-    if (resid && P.has_trace) {
-      k_trace_fix<<<1, 32, 0, c->stream>>>(resid + (m - 1), nullptr, c->d_scal + S_PRE, -b_tr);
-      HL_CHECK_LAUNCH(c);
-    }
+    launch_grad(c, U, ld, rank, pk, beta, c->d_colsum, GradOut{W, resid, nullptr});
+    if (resid && P.has_trace) trace_fix(resid, nullptr, c->d_scal + S_PRE, -b_tr);
     R.grad_evals++;
   }
   GradScal grad_read() const {
@@ -170,15 +192,11 @@ struct Solver {
     return s;
   }
   // enqueue: g(Y) - g(X) pieces (rY = A(YY^T) - b when rY != null)
-  void change_enqueue(const void* X, const void* Yv, const double* rXv, double* rYv) {
+  void change_enqueue(const void* X, const void* Yv, const void* rXv, void* rYv) {
     if (P.C_J != 0.0)
       launch_colsum_diff(c, X, Yv, ld, c->d_colsum + kColsumMax, c->d_colsum + 2 * kColsumMax);
-    launch_value_change(c, X, Yv, ld, rank, p, rXv, rYv);
-    if (rYv && P.has_trace) {
-      k_trace_fix<<<1, 32, 0, c->stream>>>(rYv + (m - 1), rXv + (m - 1), c->d_scal + S_DIFF + 3,
-                                            0.0);
-      HL_CHECK_LAUNCH(c);
-    }
+    launch_value_change(c, X, Yv, ld, rank, pk, rXv, rYv);
+    if (rYv && P.has_trace) trace_fix(rYv, rXv, c->d_scal + S_DIFF + 3, 0.0);
     R.value_evals++;
   }
   double change_read(double nrmX2) const {
@@ -345,6 +363,7 @@ struct Solver {
     launch_norm2(c, Ytil, ld, S_VEC);
     if (p0d) HL_CUDA(cudaMemcpyAsync(p, p0d, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     else HL_CUDA(cudaMemsetAsync(p, 0, m * sizeof(double), c->stream));
+    refresh_pk();
     fetch();
     const double nU = std::sqrt(c->h_scal[S_VEC]);
     if (nU > tauv) launch_scale(c, Ytil, ld, tauv / nU);
@@ -375,7 +394,7 @@ struct Solver {
         R.hlr_iters++;
         aipp(rho_t, &gs);                                           // step 6
         launch_dot(c, Wy, Ytil, ld, S_VEC);                         // G . YY^T = <GY, Y>
-        launch_dvec(c, 0, m, pshift, p, rY, beta, -1);              // p' = p + beta r(Y)
+        launch_axpy_t(c, m, pshift, p, rY, beta);                   // p' = p + beta r(Y)
         const uint64_t sd = o.seed + 7919ull * (uint64_t)R.hlr_iters;
         launch_splitmix(c, sd, v0, 0.1 / std::sqrt((double)n), have_vprev ? vprev : nullptr);
         fetch();
@@ -426,7 +445,8 @@ struct Solver {
         check_time();
       }
       // U_t = Y; dual update p_t = p + beta r (step 14)
-      launch_dvec(c, 0, m, p, p, rY, beta, -1);
+      launch_axpy_t(c, m, p, p, rY, beta);
+      refresh_pk();
       if (P.has_trace) p_tr += beta * (gs.nrm2 - b_tr);
       launch_dvec(c, 1, m, nullptr, P.b, p, 0.0, S_VEC2 + 4);
       fetch();
