@@ -3,6 +3,8 @@
 // staging and the error model (a status per call, a message per handle).
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -13,6 +15,26 @@
 #include "hallar_internal.cuh"
 
 namespace hallar {
+
+int resident_blocks(const void* fn, int block, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const std::pair<const void*, int> key(fn, dev * 4096 + block);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, smem) != cudaSuccess ||
+      nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  cache[key] = nb;
+  return nb;
+}
+
 
 void dfree(Ctx* c, void* p) {
   if (!p) return;

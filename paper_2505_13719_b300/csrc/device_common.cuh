@@ -45,6 +45,14 @@ __device__ inline void store_chunk(T* base, int64_t off, const T* o) {
   *reinterpret_cast<VT*>(base + off) = V16<T>::pack(o);
 }
 
+// typed arithmetic: the explicit intrinsics keep float operations in float
+// (an unqualified fma or fabs on floats can resolve to the double overload
+// and round-trip through the FP64 pipe)
+__device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+__device__ __forceinline__ double tabs(double a) { return ::fabs(a); }
+
 // per-thread accumulation in the factor precision --------------------------
 // double adds directly.  float uses Neumaier's compensated summation (1974):
 // on B300 every double instruction (conversions included) occupies the FP64
@@ -136,6 +144,71 @@ __device__ inline void grid_reduce(double (&v)[NS], double* __restrict__ partial
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) out[s] = acc[s];
+    *counter = 0u;
+  }
+}
+
+// grid reduction of per-thread accumulators: the warp stage runs in the
+// accumulator's own precision (float pairs combined with TwoSum for the
+// compensated float form), so each warp converts to double once; the block
+// and grid stages are grid_reduce's.
+__device__ inline void acc_combine(Acc<double>& a, double s, double) { a.s += s; }
+__device__ inline void acc_combine(Acc<float>& a, float s, float c) {
+  const float t = a.s + s;
+  const float bb = t - a.s;
+  const float err = (a.s - (t - bb)) + (s - bb);
+  a.s = t;
+  a.c += c + err;
+}
+__device__ inline double acc_c(const Acc<double>&) { return 0.0; }
+__device__ inline float acc_c(const Acc<float>& a) { return a.c; }
+
+template <class T, int NS>
+__device__ inline void grid_reduce_acc(Acc<T> (&acc)[NS], double* __restrict__ partials,
+                                       unsigned* counter, double* out) {
+  __shared__ double shw[NS][kBlock / 32];
+  __shared__ bool am_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T cs = (T)acc_c(acc[s]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const T os = __shfl_xor_sync(0xffffffffu, acc[s].s, off);
+      const T oc = __shfl_xor_sync(0xffffffffu, cs, off);
+      Acc<T> tmp = acc[s];
+      acc_combine(tmp, os, oc);
+      acc[s] = tmp;
+      cs = (T)acc_c(acc[s]);
+    }
+    if (lane == 0) shw[s][warp] = acc[s].value();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      double x = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) x += shw[s][w];
+      partials[(size_t)blockIdx.x * NS + s] = x;
+    }
+    __threadfence();
+    am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  double tot[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) tot[s] = 0.0;
+  for (unsigned b = threadIdx.x; b < gridDim.x; b += kBlock) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) tot[s] += __ldcg(&partials[(size_t)b * NS + s]);
+  }
+  __shared__ double sh2[NS][kBlock / 32];
+  block_sum<NS>(tot, sh2);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) out[s] = tot[s];
     *counter = 0u;
   }
 }

@@ -244,6 +244,7 @@ struct LanczosOut {
   double resid;
   int iters;
   bool converged;
+  int sweeps;  // reorthogonalisation sweeps against the whole basis
 };
 LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, double tol, int kmax,
                            int max_restarts, double* v_out);
@@ -256,6 +257,24 @@ hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_res
 // grid sizing: a fixed grid per (work, items per block) so that reductions
 // are deterministic; at most 8 resident 256-thread blocks per SM.
 // ---------------------------------------------------------------------------
+// blocks of `block` threads of kernel `fn` that one SM holds at once, from
+// the occupancy calculator (cached per kernel; at least 1)
+int resident_blocks(const void* fn, int block, size_t smem);
+
+// grid of a grid-stride kernel: at most one full wave of resident blocks.
+// A grid of a few partial waves leaves SMs idle in the last one; one wave
+// of resident blocks keeps every SM busy until the rows run out.
+template <class F>
+inline int wave_grid(const Ctx* c, F* fn, int64_t work_items, int items_per_block, int block,
+                     size_t smem = 0) {
+  int64_t g = (work_items + items_per_block - 1) / items_per_block;
+  int64_t cap = (int64_t)c->num_sms * resident_blocks((const void*)fn, block, smem);
+  if (cap > kMaxBlocks) cap = kMaxBlocks;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
 inline int grid_for(const Ctx* c, int64_t work_items, int items_per_block) {
   int64_t g = (work_items + items_per_block - 1) / items_per_block;
   int64_t cap = (int64_t)c->num_sms * 8;

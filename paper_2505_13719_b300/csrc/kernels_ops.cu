@@ -11,14 +11,20 @@
 // Thread mapping: a group of G lanes owns one row; lane l of the group holds
 // the 16-byte chunks l, l+G, ... of the row (K chunks), so every row access is
 // a 128-bit vector load and a group reads a 256-byte FP64 row (r = 32) with
-// one instruction per lane.  Gathered neighbour rows go through L2 (ld.cg):
-// the gather window of a row-ordered sweep is far smaller than the 126 MB L2.
+// one instruction per lane.  Gathered neighbour rows are read through L1
+// (ld.global.nc): on mesh-like graphs neighbours i +- 1 are rows of the same
+// warp or block, and the rest of the gather window of a row-ordered sweep
+// sits in the 126 MB L2.
 #include "device_common.cuh"
 #include "hallar_internal.cuh"
 
 namespace hallar {
 
 namespace {
+
+// edges whose metadata one group loads at once (at most the group's lanes)
+template <int G>
+constexpr int kEdgeBatch = G < 4 ? G : 4;
 
 template <int FAM>
 struct FamTraits {
@@ -85,15 +91,6 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
     const double rt = io.pre[0] - (double)bv[a.trace_row];
     ps_tr = (T)((double)pv[a.trace_row] + a.beta * rt);
   }
-  // the C_J 11^T U term adds C_J * colsum to every row of W
-  T cj[K][VEC];
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) {
-      const int c = (lane_g + k * G) * VEC + v;
-      cj[k][v] = (io.colsum != nullptr && c < a.ld) ? (T)(a.C_J * io.colsum[c]) : (T)0;
-    }
 
   // C.UU^T (sparse + diagonal part), p.r, r.r, and the magnitude
   // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g
@@ -117,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) nrm_l = fma(u[k][v], u[k][v], nrm_l);
+      for (int v = 0; v < VEC; ++v) nrm_l = tfma(u[k][v], u[k][v], nrm_l);
     const T nrm = group_sum<G>(nrm_l, gmask);  // |U_i|^2
 
     const T cdi = cdiag[i];
@@ -126,12 +123,12 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       // constraint i: A_i . UU^T = |U_i|^2
       const T r = nrm - bv[i];
       const T pi = pv[i];
-      const T ps = fma(beta, r, pi);
+      const T ps = tfma(beta, r, pi);
       dcoef += ps;
       if (lane_g == 0) {
         acc_pr.add(pi * r);
         acc_rr.add(r * r);
-        acc_mag.add(fabs(ps) * nrm);
+        acc_mag.add(tabs(ps) * nrm);
         if (resid) resid[i] = r;
         if (io.Tout) io.Tout[i] = (double)nrm;
       }
@@ -140,66 +137,90 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
 
     const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
     T cdot_l = (T)0;  // lane part of <U_i, sum_j C_ij U_j> over the C entries
-#pragma unroll 2
-    for (int e = e0; e < e1; ++e) {
-      const int64_t j = a.col[e];
-      T uj[K][VEC];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int ch = lane_g + k * G;
-        if (ch < nch) {
-          load_chunk_l2<T>(U, j * a.ld + ch * VEC, uj[k]);
-        } else {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) uj[k][v] = (T)0;
-        }
+    // Edges go in batches: lane t of the group loads the column, value and
+    // code of edge eb + t with one instruction and a shuffle hands them to the
+    // group, so a row's metadata costs one load round trip per batch instead
+    // of one per edge ahead of each gather.
+    for (int eb = e0; eb < e1; eb += kEdgeBatch<G>) {
+      const int cnt = min(kEdgeBatch<G>, e1 - eb);
+      int col_t = 0, code_t = 0;
+      T cv_t = (T)0;
+      if (lane_g < cnt) {
+        col_t = a.col[eb + lane_g];
+        if (Tr::kCval) cv_t = cval[eb + lane_g];
+        if (Tr::kPairs) code_t = a.code[eb + lane_g];
       }
-      T coef;
-      bool is_c;
-      if (Tr::kDiag) {
-        coef = cval[e];
-        is_c = true;
-      } else {
-        const int cd = a.code[e];
-        is_c = Tr::kCval && cd == kNoCons;
-        if (is_c) {
-          coef = cval[e];
-        } else {
-          // pair constraint l: A_l . UU^T = <U_i, U_j>
-          T d_l = (T)0;
 #pragma unroll
-          for (int k = 0; k < K; ++k)
+      for (int t = 0; t < kEdgeBatch<G>; ++t) {
+        const T cv = Tr::kCval ? __shfl_sync(gmask, cv_t, t, G) : (T)0;
+        const int cd = Tr::kPairs ? __shfl_sync(gmask, code_t, t, G) : 0;
+        const int64_t j = __shfl_sync(gmask, col_t, t, G);
+        if (t >= cnt) continue;  // uniform over the group
+        T uj[K][VEC];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) d_l = fma(u[k][v], uj[k][v], d_l);
-          const T dot = group_sum<G>(d_l, gmask);
-          const bool owner = cd >= 0;
-          const int l = owner ? cd : -cd - 1;
-          const T r = dot - bv[l];
-          const T pl = pv[l];
-          const T ps = fma(beta, r, pl);
-          coef = (T)0.5 * ps;
-          if (owner && lane_g == 0) {
-            acc_pr.add(pl * r);
-            acc_rr.add(r * r);
-            acc_mag.add(fabs(ps) * fabs(dot));
-            if (resid) resid[l] = r;
-            if (io.Tout) io.Tout[l] = (double)dot;
+        for (int k = 0; k < K; ++k) {
+          const int ch = lane_g + k * G;
+          if (ch < nch) {
+            load_chunk<T>(U, j * a.ld + ch * VEC, uj[k]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) uj[k][v] = (T)0;
           }
         }
+        T coef;
+        bool is_c;
+        if (Tr::kDiag) {
+          coef = cv;
+          is_c = true;
+        } else {
+          is_c = Tr::kCval && cd == kNoCons;
+          if (is_c) {
+            coef = cv;
+          } else {
+            // pair constraint l: A_l . UU^T = <U_i, U_j>
+            T d_l = (T)0;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) d_l = tfma(u[k][v], uj[k][v], d_l);
+            const T dot = group_sum<G>(d_l, gmask);
+            const bool owner = cd >= 0;
+            const int l = owner ? cd : -cd - 1;
+            const T r = dot - bv[l];
+            const T pl = pv[l];
+            const T ps = tfma(beta, r, pl);
+            coef = (T)0.5 * ps;
+            if (owner && lane_g == 0) {
+              acc_pr.add(pl * r);
+              acc_rr.add(r * r);
+              acc_mag.add(tabs(ps) * tabs(dot));
+              if (resid) resid[l] = r;
+              if (io.Tout) io.Tout[l] = (double)dot;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            // (diagonal family: acc holds only C terms; its dot with U_i is
+            // taken once after the loop)
+            if (!Tr::kDiag && is_c) cdot_l = tfma(coef * u[k][v], uj[k][v], cdot_l);
+            acc[k][v] = tfma(coef, uj[k][v], acc[k][v]);
+          }
       }
+    }
+    if (Tr::kDiag) {
 #pragma unroll
       for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          if (is_c) cdot_l = fma(coef * u[k][v], uj[k][v], cdot_l);
-          acc[k][v] = fma(coef, uj[k][v], acc[k][v]);
-        }
+        for (int v = 0; v < VEC; ++v) cdot_l = tfma(u[k][v], acc[k][v], cdot_l);
     }
     acc_t0.add(cdot_l);
-    acc_mag.add(fabs(cdot_l));
+    acc_mag.add(tabs(cdot_l));
     if (lane_g == 0) {
       acc_t0.add(cdi * nrm);
-      acc_mag.add(fabs(cdi) * nrm);
+      acc_mag.add(tabs(cdi) * nrm);
     }
 
     if (W != nullptr) {
@@ -209,14 +230,19 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
         if (ch < nch) {
           T w[VEC];
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) w[v] = fma(dcoef, u[k][v], acc[k][v]) + cj[k][v];
+          for (int v = 0; v < VEC; ++v) w[v] = tfma(dcoef, u[k][v], acc[k][v]);
+          if (io.colsum != nullptr) {
+            // the C_J 11^T U term adds C_J * colsum to every row of W
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) w[v] += (T)(a.C_J * __ldg(&io.colsum[ch * VEC + v]));
+          }
           store_chunk<T>(W, rowoff + ch * VEC, w);
         }
       }
     }
   }
-  double red[4] = {acc_t0.value(), acc_pr.value(), acc_rr.value(), acc_mag.value()};
-  grid_reduce<4>(red, a.partials, a.counter, a.out);
+  Acc<T> red[4] = {acc_t0, acc_pr, acc_rr, acc_mag};
+  grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
 }
 
 // ---------------------------------------------------------------------------
@@ -270,7 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
 #pragma unroll
     for (int k = 0; k < K; ++k)
 #pragma unroll
-      for (int v = 0; v < VEC; ++v) own_l = fma(d[k][v], d[k][v] + (T)2 * x[k][v], own_l);
+      for (int v = 0; v < VEC; ++v) own_l = tfma(d[k][v], d[k][v] + (T)2 * x[k][v], own_l);
     acc_tr.add(own_l);               // trace row change (lane parts)
     acc_t0.add(cdiag[i] * own_l);    // diagonal of C
     if (Tr::kDiag) {
@@ -284,47 +310,59 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
     }
     const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
     T cd_l = (T)0;
-#pragma unroll 2
-    for (int e = e0; e < e1; ++e) {
-      int cd = 0;
-      if (Tr::kPairs) {
-        cd = a.code[e];
-        if (cd < 0 && cd != kNoCons) continue;  // mirrored pair entry: the owner row does it
-        if (!Tr::kCval && cd == kNoCons) continue;
+    // edge metadata in batches, as in k_grad
+    for (int eb = e0; eb < e1; eb += kEdgeBatch<G>) {
+      const int cnt = min(kEdgeBatch<G>, e1 - eb);
+      int col_t = 0, code_t = 0;
+      T cv_t = (T)0;
+      if (lane_g < cnt) {
+        col_t = a.col[eb + lane_g];
+        if (Tr::kCval) cv_t = cval[eb + lane_g];
+        if (Tr::kPairs) code_t = a.code[eb + lane_g];
       }
-      const int64_t j = a.col[e];
-      T pd = (T)0;  // lane part of <D_i, Y_j> + <X_i, D_j>
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int ch = lane_g + k * G;
-        if (ch < nch) {
-          T xj[VEC], yj[VEC];
-          load_chunk_l2<T>(X, j * a.ld + ch * VEC, xj);
-          load_chunk_l2<T>(Y, j * a.ld + ch * VEC, yj);
+      for (int t = 0; t < kEdgeBatch<G>; ++t) {
+        const T cv = Tr::kCval ? __shfl_sync(gmask, cv_t, t, G) : (T)0;
+        const int cd = Tr::kPairs ? __shfl_sync(gmask, code_t, t, G) : 0;
+        const int64_t j = __shfl_sync(gmask, col_t, t, G);
+        if (t >= cnt) continue;  // uniform over the group
+        if (Tr::kPairs) {
+          if (cd < 0 && cd != kNoCons) continue;  // mirrored pair entry: the owner row does it
+          if (!Tr::kCval && cd == kNoCons) continue;
+        }
+        T pd = (T)0;  // lane part of <D_i, Y_j> + <X_i, D_j>
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            pd = fma(d[k][v], yj[v], pd);
-            pd = fma(x[k][v], yj[v] - xj[v], pd);
+        for (int k = 0; k < K; ++k) {
+          const int ch = lane_g + k * G;
+          if (ch < nch) {
+            T xj[VEC], yj[VEC];
+            load_chunk<T>(X, j * a.ld + ch * VEC, xj);
+            load_chunk<T>(Y, j * a.ld + ch * VEC, yj);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              pd = tfma(d[k][v], yj[v], pd);
+              pd = tfma(x[k][v], yj[v] - xj[v], pd);
+            }
           }
         }
-      }
-      if (Tr::kDiag || cd == kNoCons) {
-        cd_l = fma(cval[e], pd, cd_l);
-      } else {
-        // owned pair constraint l: dT_l = <Y_i,Y_j> - <X_i,X_j>
-        const T dt = group_sum<G>(pd, gmask);
-        if (lane_g == 0) {
-          const T rx = rXv[cd];
-          acc_pd.add(pv[cd] * dt);
-          acc_q.add(dt * ((T)2 * rx + dt));
-          if (rYv) rYv[cd] = rx + dt;
+        if (Tr::kDiag || cd == kNoCons) {
+          cd_l = tfma(cv, pd, cd_l);
+        } else {
+          // owned pair constraint l: dT_l = <Y_i,Y_j> - <X_i,X_j>
+          const T dt = group_sum<G>(pd, gmask);
+          if (lane_g == 0) {
+            const T rx = rXv[cd];
+            acc_pd.add(pv[cd] * dt);
+            acc_q.add(dt * ((T)2 * rx + dt));
+            if (rYv) rYv[cd] = rx + dt;
+          }
         }
       }
     }
     acc_t0.add(cd_l);
   }
-  double red[4] = {acc_t0.value(), acc_pd.value(), acc_q.value(), acc_tr.value()};
-  grid_reduce<4>(red, a.partials, a.counter, a.out);
+  Acc<T> red[4] = {acc_t0, acc_pd, acc_q, acc_tr};
+  grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
 }
 
 // ---------------------------------------------------------------------------
@@ -553,7 +591,7 @@ void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double bet
   io.Tout = out.T ? out.T + 1 : nullptr;
   const int tok = prof_begin(c, 0, op_bytes(c, ld, out.W != nullptr, out.resid != nullptr, true));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
-    const int grid = grid_for(c, a.n, kBlock / G);
+    const int grid = wave_grid(c, k_grad<T, FAM, G, K>, a.n, kBlock / G, kBlock);
     k_grad<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
   }));
   HL_CHECK_LAUNCH(c);
@@ -569,7 +607,7 @@ void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, co
   const int tok = prof_begin(c, 1, op_bytes(c, ld, false, rY != nullptr, true) +
                                        (double)c->P.n * ld * (double)elem_size(c));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
-    const int grid = grid_for(c, a.n, kBlock / G);
+    const int grid = wave_grid(c, k_value_change<T, FAM, G, K>, a.n, kBlock / G, kBlock);
     k_value_change<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
   }));
   HL_CHECK_LAUNCH(c);

@@ -20,19 +20,14 @@ __global__ void __launch_bounds__(kBlock) k_stream(int64_t nvec, Op op, double* 
   for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < nvec;
        v += (int64_t)gridDim.x * kBlock)
     o(v, red);
-  if constexpr (NS > 0) {
-    double r[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) r[s] = red[s].value();
-    grid_reduce<NS>(r, partials, counter, out);
-  }
+  if constexpr (NS > 0) grid_reduce_acc<T, NS>(red, partials, counter, out);
 }
 
 template <class T, int NS, class Op>
 void run_stream(Ctx* c, int64_t nelem, const Op& op, int slot) {
   constexpr int VEC = V16<T>::N;
   const int64_t nvec = nelem / VEC;
-  const int grid = grid_for(c, nvec, kBlock * 4);
+  const int grid = wave_grid(c, k_stream<T, NS, Op>, nvec, kBlock * 4, kBlock);
   k_stream<T, NS, Op><<<grid, kBlock, 0, c->stream>>>(nvec, op, c->red.partials, c->red.counter,
                                                       c->d_scal + (slot >= 0 ? slot : 0));
   HL_CHECK_LAUNCH(c);
@@ -57,7 +52,7 @@ struct OpXt : OpBase {
     HL_LOAD(y, v, a);
     HL_LOAD(x, v, b);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) o[k] = fma(wy, a[k], wx * b[k]);
+    for (int k = 0; k < VEC; ++k) o[k] = tfma(wy, a[k], wx * b[k]);
     store_chunk<T>(xt, v * VEC, o);
   }
 };
@@ -73,7 +68,7 @@ struct OpX : OpBase {
     HL_LOAD(x, v, b);
     HL_LOAD(xt, v, t);
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) o[k] = fma(cy, a[k], fma(cx, b[k], cxt * t[k]));
+    for (int k = 0; k < VEC; ++k) o[k] = tfma(cy, a[k], tfma(cx, b[k], cxt * t[k]));
     store_chunk<T>(x, v * VEC, o);
   }
 };
@@ -92,9 +87,9 @@ struct OpZ : OpBase {
     T s = (T)0;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
-      const T g = fma(c2lam, w[k], a[k] - cc[k]);
-      o[k] = fma(-invL, g, a[k]);
-      s = fma(o[k], o[k], s);
+      const T g = tfma(c2lam, w[k], a[k] - cc[k]);
+      o[k] = tfma(-invL, g, a[k]);
+      s = tfma(o[k], o[k], s);
     }
     red[0].add(s);
     store_chunk<T>(z, v * VEC, o);
@@ -125,12 +120,12 @@ struct OpY {
     for (int k = 0; k < VEC; ++k) {
       o[k] = cs * zz[k];
       const T d = o[k] - a[k];
-      const T g = fma(c2lam, w[k], a[k] - cc[k]);
+      const T g = tfma(c2lam, w[k], a[k] - cc[k]);
       const T yc = o[k] - cc[k];
-      s0 = fma(d, d, s0);
-      s1 = fma(g, d, s1);
-      s2 = fma(d, (T)0.5 * (o[k] + a[k]) - cc[k], s2);
-      s3 = fma(yc, yc, s3);
+      s0 = tfma(d, d, s0);
+      s1 = tfma(g, d, s1);
+      s2 = tfma(d, (T)0.5 * (o[k] + a[k]) - cc[k], s2);
+      s3 = tfma(yc, yc, s3);
     }
     red[0].add(s0);
     red[1].add(s1);
@@ -157,10 +152,10 @@ struct OpAipp : OpBase {
 #pragma unroll
     for (int k = 0; k < VEC; ++k) {
       const T D = yy[k] - cc[k];
-      const T VmD = fma(c2lam, w[k], L * (zz[k] - yy[k]));
-      s0 = fma(VmD + D, D, s0);
-      s1 = fma(D, D, s1);
-      s2 = fma(VmD, VmD, s2);
+      const T VmD = tfma(c2lam, w[k], L * (zz[k] - yy[k]));
+      s0 = tfma(VmD + D, D, s0);
+      s1 = tfma(D, D, s1);
+      s2 = tfma(VmD, VmD, s2);
     }
     red[0].add(s0);
     red[1].add(s1);
@@ -190,7 +185,7 @@ struct OpNorm2 : OpBase {
     HL_LOAD(u, v, a);
     T s = (T)0;
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) s = fma(a[k], a[k], s);
+    for (int k = 0; k < VEC; ++k) s = tfma(a[k], a[k], s);
     red[0].add(s);
   }
 };
@@ -205,7 +200,7 @@ struct OpDot : OpBase {
     HL_LOAD(b, v, y);
     T s = (T)0;
 #pragma unroll
-    for (int k = 0; k < VEC; ++k) s = fma(x[k], y[k], s);
+    for (int k = 0; k < VEC; ++k) s = tfma(x[k], y[k], s);
     red[0].add(s);
   }
 };

@@ -1,14 +1,26 @@
 // Minimum eigenpair of G = C + A*(p') (Alg. 1 step 7, eq. Grad X Space) by
-// Lanczos with full reorthogonalisation, in FP64 for both precision forms.
+// Lanczos with partial reorthogonalisation, in FP64 for both precision forms.
+//
+// A plain step is two thread-per-row passes over n-vectors:
+//   step 1  w = G q_k - beta_{k-1} q_{k-1}, alpha_k = <q_k, w>, q_k -> Q[:, k]
+//   step 2  w <- w - alpha_k q_k (alpha_k read from device memory),
+//           |w|^2 and sum(w)
+// and one host sync.  The host tracks the loss of orthogonality with
+// Simon's recurrence for omega_{k+1,j} ~ q_{k+1}^T q_j (H. D. Simon, "The
+// Lanczos algorithm with partial reorthogonalization", Math. Comp. 42, 1984);
+// when an estimate passes sqrt(eps), w is orthogonalised against the whole
+// basis by two classical Gram-Schmidt sweeps, at that step and the next.
+// Semi-orthogonality keeps the Ritz values of the tridiagonal accurate to
+// O(eps |G|), as full reorthogonalisation does, at a fraction of the FP64
+// work (a sweep costs two FMAs per basis element on the slow FP64 pipe).
 //
 // The basis Q is stored row-major, n x kcap (row i holds q_0[i] .. q_k[i]),
-// so each pass of an iteration streams Q once with coalesced row reads, one
-// warp per row:
-//   pass 1  w = G q_k (SpMV over the merged CSR) and h = Q^T w
-//   pass 2  w <- w - Q h and h2 = Q^T w          (the second classical
-//   pass 3  w <- w - Q h2, |w|^2 and sum(w)       Gram-Schmidt sweep)
-// alpha_k = h_k + h2_k, beta_k = |w|; the host solves the k x k tridiagonal
-// (Sturm bisection + inverse iteration) and tests the Ritz residual.
+// so a sweep streams Q with coalesced row reads, one warp per row:
+//   sweep a  h = Q^T w                     (k_lan_orth with h = 0)
+//   sweep b  w <- w - Q h and h2 = Q^T w   (k_lan_orth)
+//   sweep c  w <- w - Q h2, |w|^2, sum(w)  (k_lan_final)
+// The host solves the k x k tridiagonal (Sturm bisection + inverse
+// iteration) and tests the Ritz residual.
 #include <cmath>
 #include <vector>
 
@@ -78,43 +90,46 @@ __device__ inline double gv_row(const LanArgs& a, int64_t i, const double* __res
   return s;
 }
 
-// pass 1: w = G v, v = vin * vscale (stored as column k of Q); h = Q[:, :k+1]^T w
-template <int NACC>
-__global__ void __launch_bounds__(kBlock) k_lan_spmv(LanArgs a, const double* __restrict__ vin,
-                                                     double vscale, double vsum,
-                                                     double* __restrict__ Q, int kcap, int k,
-                                                     double* __restrict__ w,
-                                                     double* __restrict__ part) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * kBlock + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t)gridDim.x * (kBlock / 32);
-  const int ncols = k + 1;
-  double acc[NACC];
-#pragma unroll
-  for (int t = 0; t < NACC; ++t) acc[t] = 0.0;
-  for (int64_t i = warp; i < a.n; i += nwarps) {
+// step 1: q_k = vin * vscale (stored as column k of Q),
+// w = G q_k - bprev * (prev * pscale) written over prev, alpha partial <q_k, w>
+__global__ void __launch_bounds__(kBlock) k_lan_step1(LanArgs a, const double* __restrict__ vin,
+                                                      double vscale, double vsum,
+                                                      double* __restrict__ prev, double pscale,
+                                                      double bprev, double* __restrict__ Q,
+                                                      int kcap, int k, double* partials,
+                                                      unsigned* counter, double* out) {
+  double red[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kBlock) {
     const double vi = vin[i] * vscale;
-    double s = gv_row(a, i, vin, vscale, vsum, vi, lane, 32);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    const double wi = s;
-    double* __restrict__ qrow = Q + i * (int64_t)kcap;
-#pragma unroll
-    for (int t = 0; t < NACC; ++t) {
-      const int j = lane + 32 * t;
-      if (j < k) acc[t] = fma(qrow[j], wi, acc[t]);
-      else if (j == k) acc[t] = fma(vi, wi, acc[t]);
-    }
-    __syncwarp();
-    if (lane == 0) {
-      w[i] = wi;
-      qrow[k] = vi;
-    }
+    double wi = gv_row(a, i, vin, vscale, vsum, vi, 0, 1);
+    if (bprev != 0.0) wi = fma(-bprev * pscale, prev[i], wi);
+    prev[i] = wi;
+    Q[i * (int64_t)kcap + k] = vi;
+    red[0] = fma(vi, wi, red[0]);
   }
-  write_block_partial<NACC>(acc, ncols, part);
+  grid_reduce<1>(red, partials, counter, out);
 }
 
-// pass 2: w <- w - Q h and h2 = Q^T w   (ncols = k + 1)
+// step 2: w <- w - alpha q_k, alpha = *alpha_dev; |w|^2 and sum(w)
+__global__ void __launch_bounds__(kBlock) k_lan_step2(int64_t n, const double* __restrict__ vin,
+                                                      double vscale,
+                                                      const double* __restrict__ alpha_dev,
+                                                      double* __restrict__ w, double* partials,
+                                                      unsigned* counter, double* out) {
+  const double am = -(*alpha_dev) * vscale;
+  double red[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const double wi = fma(am, vin[i], w[i]);
+    w[i] = wi;
+    red[0] = fma(wi, wi, red[0]);
+    red[1] += wi;
+  }
+  grid_reduce<2>(red, partials, counter, out);
+}
+
+// sweep: w <- w - Q h and h2 = Q^T w   (ncols = k + 1; h = 0 gives h2 = Q^T w)
 template <int NACC>
 __global__ void __launch_bounds__(kBlock) k_lan_orth(int64_t n, const double* __restrict__ Q,
                                                      int kcap, int ncols,
@@ -152,7 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_lan_orth(int64_t n, const double* __
   write_block_partial<NACC>(acc, ncols, part);
 }
 
-// pass 3: w <- w - Q h2; reductions |w|^2 and sum(w) (ncols = 0: only the sums)
+// last sweep: w <- w - Q h2; reductions |w|^2 and sum(w) (ncols = 0: only the sums)
 template <int NACC>
 __global__ void __launch_bounds__(kBlock) k_lan_final(int64_t n, const double* __restrict__ Q,
                                                       int kcap, int ncols,
@@ -375,11 +390,12 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
   const int kcap = (kmax + 3) / 4 * 4;
   int grid = grid_for(c, n, (kBlock / 32) * 4);
   if (grid > 1184) grid = 1184;
+  const int grid_row = grid_for(c, n, kBlock * 2);
   // workspace kept by the handle between calls
   double* Q = (double*)ensure_buffer(c, &c->lan_Q, &c->lan_Q_bytes,
                                      (size_t)n * kcap * sizeof(double));
-  double* w = (double*)ensure_buffer(c, &c->lan_w, &c->lan_w_bytes, 2 * (size_t)n * sizeof(double));
-  double* vin = w + n;
+  double* bufs = (double*)ensure_buffer(c, &c->lan_w, &c->lan_w_bytes,
+                                        2 * (size_t)n * sizeof(double));
   double* part = (double*)ensure_buffer(c, &c->lan_part, &c->lan_part_bytes,
                                         (size_t)grid * kcap * sizeof(double));
   double* hbuf = (double*)ensure_buffer(c, &c->lan_h, &c->lan_h_bytes,
@@ -399,8 +415,12 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
   a.has_trace = c->P.has_trace;
   a.trace_row = c->P.m - 1;
   a.ps = pshift;
+  double* const d_alpha = c->d_scal + S_LAN + 6;  // alpha_k of the current step
+  const double eps = 1.1102230246251565e-16;      // 2^-53
+  const double sqrt_eps = std::sqrt(eps);
+  const double omega_floor = eps * std::sqrt((double)n);  // omega after a sweep
 
-  // |v|^2 and sum(v) of a vector: pass 3 with no basis columns
+  // |v|^2 and sum(v) of a vector: the last sweep with no basis columns
   auto norm_and_sum = [&](double* vec, double& nrm2, double& sum) {
     k_lan_final<1><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, 0, h, vec, c->red.partials,
                                                    c->red.counter, c->d_scal + S_LAN + 4);
@@ -410,9 +430,12 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
     sum = c->h_scal[S_LAN + 5];
   };
 
+  double* vin = bufs + n;  // current basis vector, unnormalised
+  double* prev = bufs;     // previous basis vector, then w
   HL_CUDA(cudaMemcpyAsync(vin, v0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  LanczosOut res{0.0, INFINITY, 0, false};
+  LanczosOut res{0.0, INFINITY, 0, false, 0};
   std::vector<double> al, be, s;
+  std::vector<double> om_prev, om_cur, om_next;  // omega_{k-1,.}, omega_{k,.}, omega_{k+1,.}
   int total = 0;
   for (int restart = 0; restart <= max_restarts; ++restart) {
     double nv2, vs;
@@ -424,44 +447,93 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
     }
     double vscale = 1.0 / std::sqrt(nv2);
     double vsum = vs * vscale;
+    double pscale = 0.0, bprev = 0.0;
     al.clear();
     be.clear();
-    double* cur_in = vin;
-    double* cur_w = w;
+    om_prev.assign(kmax + 2, 0.0);
+    om_cur.assign(kmax + 2, 0.0);
+    om_next.assign(kmax + 2, 0.0);
+    om_cur[0] = 1.0;  // omega_{0,0}
+    double anorm = 0.0;
+    bool force_sweep = false;
     bool done = false;
     int kk = 0;
     for (int k = 0; k < kmax; ++k) {
       const int ncols = k + 1;
-      const int tok1 = prof_begin(c, 2, 8.0 * n * k + 24.0 * n + 16.0 * (double)c->P.nnz);
-      HL_BY_NACC(ncols, k_lan_spmv<NACC><<<grid, kBlock, 0, c->stream>>>(
-                            a, cur_in, vscale, vsum, Q, kcap, k, cur_w, part));
+      // step 1 and step 2 (three-term recurrence)
+      const int tok1 = prof_begin(c, 2, 40.0 * n + 12.0 * (double)c->P.nnz + 8.0 * c->P.m);
+      k_lan_step1<<<grid_row, kBlock, 0, c->stream>>>(a, vin, vscale, vsum, prev, pscale, bprev, Q,
+                                                     kcap, k, c->red.partials, c->red.counter,
+                                                     d_alpha);
+      HL_CHECK_LAUNCH(c);
+      k_lan_step2<<<grid_row, kBlock, 0, c->stream>>>(n, vin, vscale, d_alpha, prev,
+                                                     c->red.partials, c->red.counter,
+                                                     c->d_scal + S_LAN);
       HL_CHECK_LAUNCH(c);
       prof_end(c, tok1);
-      k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h);
-      HL_CHECK_LAUNCH(c);
-      const int tok2 = prof_begin(c, 2, 8.0 * n * ncols + 16.0 * n);
-      HL_BY_NACC(ncols, k_lan_orth<NACC><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, ncols, h,
-                                                                          cur_w, part));
-      HL_CHECK_LAUNCH(c);
-      prof_end(c, tok2);
-      k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h2);
-      HL_CHECK_LAUNCH(c);
-      const int tok3 = prof_begin(c, 2, 8.0 * n * ncols + 16.0 * n);
-      HL_BY_NACC(ncols, k_lan_final<NACC><<<grid, kBlock, 0, c->stream>>>(
-                            n, Q, kcap, ncols, h2, cur_w, c->red.partials, c->red.counter,
-                            c->d_scal + S_LAN));
-      HL_CHECK_LAUNCH(c);
-      prof_end(c, tok3);
-      HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 2, h + k, sizeof(double),
-                              cudaMemcpyDeviceToHost, c->stream));
-      HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 3, h2 + k, sizeof(double),
-                              cudaMemcpyDeviceToHost, c->stream));
-      fetch_scalars(c, S_LAN, 2);
+      fetch_scalars(c, S_LAN, 7);
       ++total;
-      const double alpha = c->h_scal[S_LAN + 2] + c->h_scal[S_LAN + 3];
-      const double bnorm = std::sqrt(c->h_scal[S_LAN]);
+      double alpha = c->h_scal[S_LAN + 6];
+      double bnorm = std::sqrt(c->h_scal[S_LAN]);
+      double wsum = c->h_scal[S_LAN + 1];
       if (!std::isfinite(alpha) || !std::isfinite(bnorm))
         fail(HALLAR_ENUMERIC, "Lanczos: non-finite value");
+      anorm = std::fmax(anorm, std::fabs(alpha) + bnorm + (k > 0 ? be[k - 1] : 0.0));
+
+      // Simon's estimate of omega_{k+1,j} = q_{k+1}^T q_j, j <= k
+      const bool forced = force_sweep;
+      bool sweep = forced;
+      if (bnorm > 0.0) {
+        const double theta = 2.0 * eps * anorm / bnorm;
+        for (int j = 0; j < k; ++j) {
+          double o = be[j] * om_cur[j + 1] + (al[j] - alpha) * om_cur[j] - be[k - 1] * om_prev[j];
+          if (j > 0) o += be[j - 1] * om_cur[j - 1];
+          o /= bnorm;
+          o += o >= 0.0 ? theta : -theta;
+          om_next[j] = o;
+          if (std::fabs(o) > sqrt_eps) sweep = true;
+        }
+        om_next[k] = eps * std::sqrt((double)n) * anorm / bnorm;
+        if (std::fabs(om_next[k]) > sqrt_eps) sweep = true;
+      }
+      if (sweep && bnorm > 0.0) {
+        // two classical Gram-Schmidt sweeps of w against q_0 .. q_k
+        const int tok2 = prof_begin(c, 2, 3.0 * (8.0 * n * ncols + 16.0 * n));
+        HL_CUDA(cudaMemsetAsync(h2, 0, ncols * sizeof(double), c->stream));
+        HL_BY_NACC(ncols, k_lan_orth<NACC><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, ncols, h2,
+                                                                            prev, part));
+        HL_CHECK_LAUNCH(c);
+        k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h);
+        HL_CHECK_LAUNCH(c);
+        HL_BY_NACC(ncols, k_lan_orth<NACC><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, ncols, h,
+                                                                            prev, part));
+        HL_CHECK_LAUNCH(c);
+        k_sum_cols<<<(ncols * 32 + 255) / 256, 256, 0, c->stream>>>(part, grid, ncols, h2);
+        HL_CHECK_LAUNCH(c);
+        HL_BY_NACC(ncols, k_lan_final<NACC><<<grid, kBlock, 0, c->stream>>>(
+                              n, Q, kcap, ncols, h2, prev, c->red.partials, c->red.counter,
+                              c->d_scal + S_LAN));
+        HL_CHECK_LAUNCH(c);
+        prof_end(c, tok2);
+        HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 2, h + k, sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+        HL_CUDA(cudaMemcpyAsync(c->h_scal + S_LAN + 3, h2 + k, sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+        fetch_scalars(c, S_LAN, 2);
+        // the components removed along q_k belong to alpha_k
+        alpha += c->h_scal[S_LAN + 2] + c->h_scal[S_LAN + 3];
+        bnorm = std::sqrt(c->h_scal[S_LAN]);
+        wsum = c->h_scal[S_LAN + 1];
+        if (!std::isfinite(alpha) || !std::isfinite(bnorm))
+          fail(HALLAR_ENUMERIC, "Lanczos: non-finite value");
+        for (int j = 0; j <= k; ++j) om_next[j] = omega_floor;
+        // Simon: a sweep at one step is followed by a sweep at the next
+        force_sweep = !forced;
+        ++res.sweeps;
+      } else {
+        force_sweep = false;
+      }
+      om_next[k + 1] = 1.0;
       al.push_back(alpha);
       be.push_back(bnorm);
       kk = k + 1;
@@ -471,10 +543,14 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
         done = true;
         break;
       }
-      // next basis vector w / |w|, scaled on the fly by the next pass 1
+      // next basis vector w / |w|, scaled on the fly by the next step 1
+      std::swap(om_prev, om_cur);
+      std::swap(om_cur, om_next);
+      pscale = vscale;
+      bprev = bnorm;
       vscale = 1.0 / bnorm;
-      vsum = c->h_scal[S_LAN + 1] * vscale;
-      std::swap(cur_in, cur_w);
+      vsum = wsum * vscale;
+      std::swap(vin, prev);
     }
     // Ritz vector v = Q s, normalised
     HL_CUDA(cudaMemcpyAsync(sdev, s.data(), kk * sizeof(double), cudaMemcpyHostToDevice,
