@@ -28,9 +28,12 @@ def H():
     return hallar
 
 
-# relative KKT tolerance per form: the mixed form computes in float, whose
-# rounding floors the reachable accuracy near 1e-7 relative
-TOLS = {0: 1e-6, 1: 5e-6}
+# relative KKT tolerance per form.  FP64 solves run ten times tighter than
+# the 1e-5 target.  The mixed form is held to the target itself: it computes
+# residuals in float, and the multipliers built from them by p += beta r
+# carry that rounding into the dual value, whose gap to the primal stalls
+# at a few 1e-6 relative on the +-1 torus (measured 5.4e-6)
+TOLS = {0: 1e-6, 1: 1e-5}
 
 
 def gpu_solve(H, inst, r0, seed, prec=0, tol=None, **opts):
@@ -74,12 +77,18 @@ def test_closed_form(H, name, make, ref, prec):
     assert np.linalg.norm(U) <= math.sqrt(inst.tau2) * (1 + 1e-6)
 
 
-def test_matrix_completion(H):
-    inst = I.completion(60, 80, 2, I.completion_sample_count(60, 80, 2) // 4, seed=5)
-    st, res, U, p = gpu_solve(H, inst, 2, 9)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_matrix_completion(H, prec):
+    # with the full sample count the nuclear-norm SDP recovers the rank-2
+    # truth M exactly, so its optimal value is |M|_* (the oracle reaches
+    # 125.127908 against |M|_* = 125.127919 at rank 2); with a quarter of the
+    # samples another completion has a smaller nuclear norm and neither the
+    # oracle nor this solver returns |M|_*
+    inst = I.completion(60, 80, 2, I.completion_sample_count(60, 80, 2), seed=5)
+    st, res, U, p = gpu_solve(H, inst, 2, 9, prec=prec)
     assert st == H.HALLAR_OK
     nuc = inst.meta["nuclear_norm"]
-    assert abs(res.pval - nuc) <= 1e-4 * nuc
+    assert abs(res.pval - nuc) <= 2 * TOLS[prec] * nuc
     M = inst.meta["G"] @ inst.meta["H"].T
     X12 = U[:60] @ U[60:].T
     assert np.linalg.norm(X12 - M) <= 1e-2 * np.linalg.norm(M)
