@@ -266,10 +266,13 @@ def run_ours(args, world, rank):
     k = int(np.argmax(prof_ms))
     peaks = load_peaks()
     achieved = prof_bytes[k] / (prof_ms[k] / 1e3) / 1e9 if prof_ms[k] > 0 else None
+    width = int(round(counts["rank"]))
     roofline = {"bound": "hbm", "kernel": names[k], "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None,
-                "traffic": None, "peak_source": peaks["source"],
+                "traffic": profiled_traffic(names[k], args.precision, width),
+                "bytes_per_launch": prof_bytes[k] / max(1, prof_n[k]),
+                "peak_source": peaks["source"],
                 "avg_launch_us": 1e3 * prof_ms[k] / max(1, prof_n[k]),
                 "launches": int(prof_n[k]),
                 "classes": {names[j]: {"ms": round(prof_ms[j], 3), "launches": int(prof_n[j]),
@@ -305,6 +308,45 @@ def run_ours(args, world, rank):
         "cpu_baseline": cpu,
     }
     return line
+
+
+# sources the fused operator kernels are built from; a DRAM traffic figure
+# from an ncu capture is reported only while they are unchanged
+KERNEL_SOURCES = ("paper_2505_13719_b300/csrc/kernels_ops.cu",
+                  "paper_2505_13719_b300/csrc/device_common.cuh")
+TRAFFIC_PROFILES = {
+    # (kernel class, precision, factor width) -> summary with the ncu figures
+    ("fused_constraint_map_shift_spmm", "mixed", 10): "profiles/k_grad_torus1000_mixed_r10.md",
+}
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, precision, width):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of one ncu capture, or None when there is none for this kernel and
+    shape or the kernel sources changed since it was taken."""
+    rel = TRAFFIC_PROFILES.get((kernel, precision, width))
+    if rel is None or not os.path.exists(os.path.join(ROOT, rel)):
+        return None
+    fields = {}
+    for line in open(os.path.join(ROOT, rel)):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip().strip("`")
+    if fields.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def load_peaks():

@@ -28,12 +28,16 @@ def H():
     return hallar
 
 
-# relative KKT tolerance per form.  FP64 solves run ten times tighter than
-# the 1e-5 target.  The mixed form is held to the target itself: it computes
-# residuals in float, and the multipliers built from them by p += beta r
-# carry that rounding into the dual value, whose gap to the primal stalls
-# at a few 1e-6 relative on the +-1 torus (measured 5.4e-6)
-TOLS = {0: 1e-6, 1: 1e-5}
+# relative KKT tolerance per form.  The relative gap is normalised by
+# 1 + |pval| + |dval| (about twice the objective), so a solve stopped at
+# tolerance t has its objective within about 2t of the optimum: 5e-6 is what
+# an objective check at 1e-5 needs.  FP64 solves run at 1e-6.
+TOLS = {0: 1e-6, 1: 5e-6}
+# The mixed form computes residuals in float and the multipliers built from
+# them by p += beta r carry that rounding into the dual value: on the
+# high-rank +-1 torus its gap stalls near 5.4e-6, so that case is solved to
+# the 1e-5 KKT target itself (its objective still agrees to 1e-5)
+STORED_MIXED_TOL = {"maxcut_torus_16x16_pm1": 1e-5}
 
 
 def gpu_solve(H, inst, r0, seed, prec=0, tol=None, **opts):
@@ -88,7 +92,7 @@ def test_matrix_completion(H, prec):
     st, res, U, p = gpu_solve(H, inst, 2, 9, prec=prec)
     assert st == H.HALLAR_OK
     nuc = inst.meta["nuclear_norm"]
-    assert abs(res.pval - nuc) <= 2 * TOLS[prec] * nuc
+    assert abs(res.pval - nuc) <= 1e-5 * nuc
     M = inst.meta["G"] @ inst.meta["H"].T
     X12 = U[:60] @ U[60:].T
     assert np.linalg.norm(X12 - M) <= 1e-2 * np.linalg.norm(M)
@@ -130,7 +134,9 @@ def test_against_stored_oracle_solve(H, name, prec):
         pytest.skip(f"no stored oracle value for {name}")
     ref = stored[name]
     inst = STORED[name]()
-    st, res, U, p = gpu_solve(H, inst, ref["r0"], ref["u0_seed"], prec=prec, r_cap=ref["r_cap"])
+    tol = STORED_MIXED_TOL.get(name) if prec == 1 else None
+    st, res, U, p = gpu_solve(H, inst, ref["r0"], ref["u0_seed"], prec=prec, tol=tol,
+                              r_cap=ref["r_cap"])
     assert st == H.HALLAR_OK, res.as_dict()
     assert abs(res.pval - ref["pval"]) <= 1e-5 * abs(ref["pval"]), (res.pval, ref["pval"])
 
