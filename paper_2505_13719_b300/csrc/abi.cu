@@ -483,7 +483,7 @@ hallar_status hallar_eval_A(hallar_t h, const void* U, int32_t r, double* T) {
     if (c->P.C_J != 0.0 || c->P.has_trace) launch_colsum(c, Ud, ld, c->d_colsum, S_PRE);
     // the multipliers do not enter T: b stands in for p with beta = 0
     const void* bk = c->opt.precision == HALLAR_MIXED ? (const void*)c->P.b32 : (const void*)c->P.b;
-    launch_grad(c, Ud, ld, r, bk, 0.0, c->d_colsum, GradOut{nullptr, nullptr, Td});
+    launch_grad(c, Ud, ld, r, bk, 0.0, GradOut{nullptr, nullptr, Td});
     fetch_scalars(c, 0, S_COUNT);
     double* hs = c->h_scal + S_SCALE;
     hs[2] = c->h_scal[S_GRAD] + c->P.C_J * c->h_scal[S_PRE + 1];
@@ -531,7 +531,7 @@ hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
                         : ensure_buffer(c, &c->stage_wout, &c->stage_wout_bytes,
                                         (size_t)c->P.n * ld * elem_size(c));
     if (c->P.C_J != 0.0 || c->P.has_trace) launch_colsum(c, Ud, ld, c->d_colsum, S_PRE);
-    launch_grad(c, Ud, ld, r, pk, beta, c->d_colsum, GradOut{Wd, rk, nullptr});
+    launch_grad(c, Ud, ld, r, pk, beta, GradOut{Wd, rk, nullptr});
     if (mixed && resid) launch_to_double(c, m, rd, rk);
     fetch_scalars(c, 0, S_COUNT);
     const double* hsc = c->h_scal;

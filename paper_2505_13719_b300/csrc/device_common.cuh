@@ -82,6 +82,15 @@ __device__ inline T group_sum(T v, unsigned mask) {
   for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, G);
   return v;
 }
+// value v of lane t of the group (G = 1: the thread's own value, no shuffle)
+template <int G, class V>
+__device__ __forceinline__ V group_bcast(V v, int t, unsigned mask) {
+  if constexpr (G == 1) {
+    return v;
+  } else {
+    return __shfl_sync(mask, v, t, G);
+  }
+}
 template <int G>
 __device__ inline unsigned group_mask() {
   if (G == 32) return 0xffffffffu;

@@ -95,6 +95,7 @@ struct hallar_ctx {
   double* stage_m1 = nullptr; size_t stage_m1_bytes = 0;
   double* stage_p0 = nullptr; size_t stage_p0_bytes = 0;
   void* stage_pk = nullptr; size_t stage_pk_bytes = 0;
+  void* stage_T = nullptr; size_t stage_T_bytes = 0;     // constraint values in the factor type
   void* eig_stage = nullptr; size_t eig_stage_bytes = 0;
   void* gram_part = nullptr; size_t gram_part_bytes = 0;
   // Lanczos workspace (basis, vectors, partial rows)
@@ -186,15 +187,18 @@ struct GradOut {
 
 // algorithmic bytes of one launch of the fused operator (see kernels_ops.cu)
 double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool reads_p);
-// pre-pass: colsum of U into colsum_out, S_PRE[0] = |U|_F^2, S_PRE[1] = |colsum|^2
+// pre-pass: colsum of U into colsum_out, S_PRE[0] = |U|_F^2, S_PRE[1] = |colsum|^2,
+// and C_J * colsum in the factor type at cj_row (kColsumMax entries) when C_J != 0
 void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot);
+// where launch_colsum leaves C_J * colsum in the factor type
+inline void* cj_row(const Ctx* c) { return c->d_colsum + 3 * kColsumMax; }
 // fused A~(UU^T), shift and SpMM.  Reductions into S_GRAD:
 //   [0] C.UU^T without the C_J part, [1] sum p_l r_l, [2] sum r_l^2 (the
 //   trace row excluded), [3] sum |p'_l| |A_l.UU^T| + |sparse and diagonal
 //   C terms| (the scale of the rounding of g).
 // p has the factor's element type (float copy in the mixed form)
 void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
-                 const double* colsum, GradOut out);
+                 GradOut out);
 // g(Y) - g(X) pieces into S_DIFF: [0] dT0 (no C_J part) [1] p.dT [2] dT(2rX+dT)
 // [3] trace dT = sum <D_i, Y_i + X_i>; rY (if non-null) = rX + dT.
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r,

@@ -61,14 +61,16 @@ struct OpArgs {
 // ---------------------------------------------------------------------------
 struct GradIO {
   const void* __restrict__ U;
-  const double* __restrict__ colsum;  // [ld] or null: C_J 11^T U = 1 (colsum)^T
+  const void* __restrict__ cjv;       // T[ld] or null: C_J 11^T U = 1 (C_J colsum)^T
   const double* __restrict__ pre;     // pre[0] = |U|_F^2 (trace row)
   void* __restrict__ W;               // T, or null
   void* __restrict__ resid;           // T, or null
-  double* __restrict__ Tout;          // T[1 + l] or null
+  void* __restrict__ Tout;            // T: A_l . UU^T at [l], or null
 };
 
-template <class T, int FAM, int G, int K>
+// CJ: C has the implicit C_J 11^T part (a compile-time switch: an unused
+// runtime branch would still cost predicated instructions in the row loop)
+template <class T, int FAM, int G, int K, bool CJ>
 __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
   using Tr = FamTraits<FAM>;
   constexpr int VEC = V16<T>::N;
@@ -79,6 +81,8 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
   const T* __restrict__ pv = static_cast<const T*>(a.p);
   T* __restrict__ W = static_cast<T*>(io.W);
   T* __restrict__ resid = static_cast<T*>(io.resid);
+  T* __restrict__ Tout = static_cast<T*>(io.Tout);
+  const T* __restrict__ cjv = static_cast<const T*>(io.cjv);
   const int lane_g = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
         acc_rr.add(r * r);
         acc_mag.add(tabs(ps) * nrm);
         if (resid) resid[i] = r;
-        if (io.Tout) io.Tout[i] = (double)nrm;
+        if (Tout) Tout[i] = nrm;
       }
     }
     if (Tr::kPairs) dcoef += ps_tr;
@@ -152,9 +156,9 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       }
 #pragma unroll
       for (int t = 0; t < kEdgeBatch<G>; ++t) {
-        const T cv = Tr::kCval ? __shfl_sync(gmask, cv_t, t, G) : (T)0;
-        const int cd = Tr::kPairs ? __shfl_sync(gmask, code_t, t, G) : 0;
-        const int64_t j = __shfl_sync(gmask, col_t, t, G);
+        const T cv = Tr::kCval ? group_bcast<G>(cv_t, t, gmask) : (T)0;
+        const int cd = Tr::kPairs ? group_bcast<G>(code_t, t, gmask) : 0;
+        const int64_t j = group_bcast<G>(col_t, t, gmask);
         if (t >= cnt) continue;  // uniform over the group
         T uj[K][VEC];
 #pragma unroll
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
               acc_rr.add(r * r);
               acc_mag.add(tabs(ps) * tabs(dot));
               if (resid) resid[l] = r;
-              if (io.Tout) io.Tout[l] = (double)dot;
+              if (Tout) Tout[l] = dot;
             }
           }
         }
@@ -231,10 +235,10 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
           T w[VEC];
 #pragma unroll
           for (int v = 0; v < VEC; ++v) w[v] = tfma(dcoef, u[k][v], acc[k][v]);
-          if (io.colsum != nullptr) {
+          if constexpr (CJ) {
             // the C_J 11^T U term adds C_J * colsum to every row of W
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) w[v] += (T)(a.C_J * __ldg(&io.colsum[ch * VEC + v]));
+            for (int v = 0; v < VEC; ++v) w[v] += __ldg(&cjv[ch * VEC + v]);
           }
           store_chunk<T>(W, rowoff + ch * VEC, w);
         }
@@ -322,9 +326,9 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
       }
 #pragma unroll
       for (int t = 0; t < kEdgeBatch<G>; ++t) {
-        const T cv = Tr::kCval ? __shfl_sync(gmask, cv_t, t, G) : (T)0;
-        const int cd = Tr::kPairs ? __shfl_sync(gmask, code_t, t, G) : 0;
-        const int64_t j = __shfl_sync(gmask, col_t, t, G);
+        const T cv = Tr::kCval ? group_bcast<G>(cv_t, t, gmask) : (T)0;
+        const int cd = Tr::kPairs ? group_bcast<G>(code_t, t, gmask) : 0;
+        const int64_t j = group_bcast<G>(col_t, t, gmask);
         if (t >= cnt) continue;  // uniform over the group
         if (Tr::kPairs) {
           if (cd < 0 && cd != kNoCons) continue;  // mirrored pair entry: the owner row does it
@@ -376,7 +380,8 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
                                                    int mode, const T* __restrict__ Y,
                                                    double* partials, unsigned* counter,
                                                    double* colsum_out, double* colsum_out2,
-                                                   double* scal_out) {
+                                                   double* scal_out, double cj,
+                                                   T* __restrict__ cj_out) {
   // mode 0: s = colsum(U), scal = [|U|_F^2, |s|^2]
   // mode 1: X = U, D = Y - X: s = colsum(D), s2 = colsum(Y + X),
   //         scal = [sum <D_i, Y_i + X_i>, <s, s2>]
@@ -439,6 +444,7 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
       sh2[cc] = s2;
       colsum_out[cc] = s;
       if (colsum_out2) colsum_out2[cc] = s2;
+      if (cj_out) cj_out[cc] = (T)(cj * s);
     } else {
       scal_out[0] = s;
     }
@@ -514,8 +520,15 @@ struct Shape {
 };
 Shape pick_shape(int ld, int vec) {
   const int nch = ld / vec;
+  // narrow rows: one thread per row (K chunks each), so a warp keeps 32 rows'
+  // gathers in flight and row sums need no shuffles; rows of 6-8 chunks: four
+  // lanes of two chunks.  Measured on the 10^6-vertex torus: float r = 10
+  // 44 us (88 us with four lanes of one chunk), float r = 32 111 us (152 us
+  // with eight lanes of one chunk), double r = 10 158 us (453 us).
+  if (nch <= 5) return {1, nch};
+  if (nch <= 8) return {4, 2};
   if (nch <= 32) {
-    int G = 2;
+    int G = 8;
     while (G < nch) G <<= 1;
     return {G, 1};
   }
@@ -528,8 +541,12 @@ Shape pick_shape(int ld, int vec) {
   do {                                                                 \
     const Shape s__ = pick_shape((ld), V16<T_>::N);                    \
     switch (s__.G * 10 + s__.K) {                                      \
-      case 21: { constexpr int G = 2, K = 1; __VA_ARGS__; } break;            \
-      case 41: { constexpr int G = 4, K = 1; __VA_ARGS__; } break;            \
+      case 11: { constexpr int G = 1, K = 1; __VA_ARGS__; } break;            \
+      case 12: { constexpr int G = 1, K = 2; __VA_ARGS__; } break;            \
+      case 13: { constexpr int G = 1, K = 3; __VA_ARGS__; } break;            \
+      case 14: { constexpr int G = 1, K = 4; __VA_ARGS__; } break;            \
+      case 15: { constexpr int G = 1, K = 5; __VA_ARGS__; } break;            \
+      case 42: { constexpr int G = 4, K = 2; __VA_ARGS__; } break;            \
       case 81: { constexpr int G = 8, K = 1; __VA_ARGS__; } break;            \
       case 161: { constexpr int G = 16, K = 1; __VA_ARGS__; } break;          \
       case 321: { constexpr int G = 32, K = 1; __VA_ARGS__; } break;          \
@@ -576,26 +593,39 @@ double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool rea
 }
 
 void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
-                 const double* colsum, GradOut out) {
+                 GradOut out) {
   (void)r;
   if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
   OpArgs a = make_args(c, ld, S_GRAD);
   a.p = p;
   a.beta = beta;
+  const bool mixed = c->opt.precision == HALLAR_MIXED;
   GradIO io;
   io.U = U;
-  io.colsum = (c->P.C_J != 0.0) ? colsum : nullptr;
+  io.cjv = (c->P.C_J != 0.0) ? cj_row(c) : nullptr;
   io.pre = c->d_scal + S_PRE;
   io.W = out.W;
   io.resid = out.resid;
-  io.Tout = out.T ? out.T + 1 : nullptr;
+  // constraint values leave the kernel in the factor type (no double
+  // instructions in the row loop); the float form widens them afterwards
+  void* tout = nullptr;
+  if (out.T)
+    tout = mixed ? ensure_buffer(c, &c->stage_T, &c->stage_T_bytes, (size_t)c->P.m * sizeof(float))
+                 : (void*)(out.T + 1);
+  io.Tout = tout;
   const int tok = prof_begin(c, 0, op_bytes(c, ld, out.W != nullptr, out.resid != nullptr, true));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
-    const int grid = wave_grid(c, k_grad<T, FAM, G, K>, a.n, kBlock / G, kBlock);
-    k_grad<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
+    if (io.cjv != nullptr) {
+      const int grid = wave_grid(c, k_grad<T, FAM, G, K, true>, a.n, kBlock / G, kBlock);
+      k_grad<T, FAM, G, K, true><<<grid, kBlock, 0, c->stream>>>(a, io);
+    } else {
+      const int grid = wave_grid(c, k_grad<T, FAM, G, K, false>, a.n, kBlock / G, kBlock);
+      k_grad<T, FAM, G, K, false><<<grid, kBlock, 0, c->stream>>>(a, io);
+    }
   }));
   HL_CHECK_LAUNCH(c);
   prof_end(c, tok);
+  if (out.T && mixed) launch_to_double(c, c->P.m, out.T + 1, tout);
 }
 
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const void* p,
@@ -618,14 +648,16 @@ void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot) 
   if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
   const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
   const int grid = grid_for(c, c->P.n, rows_per_pass * 8);
+  const double cj = c->P.C_J;
+  void* cjo = cj != 0.0 ? cj_row(c) : nullptr;
   if (c->opt.precision == HALLAR_MIXED)
     k_colsum<float><<<grid, kBlock, 0, c->stream>>>(
         (const float*)U, c->P.n, ld, 0, nullptr, c->red.partials, c->red.counter, colsum_out,
-        nullptr, c->d_scal + slot);
+        nullptr, c->d_scal + slot, cj, (float*)cjo);
   else
     k_colsum<double><<<grid, kBlock, 0, c->stream>>>(
         (const double*)U, c->P.n, ld, 0, nullptr, c->red.partials, c->red.counter, colsum_out,
-        nullptr, c->d_scal + slot);
+        nullptr, c->d_scal + slot, cj, (double*)cjo);
   HL_CHECK_LAUNCH(c);
 }
 
@@ -636,11 +668,11 @@ void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD
   if (c->opt.precision == HALLAR_MIXED)
     k_colsum<float><<<grid, kBlock, 0, c->stream>>>(
         (const float*)X, c->P.n, ld, 1, (const float*)Y, c->red.partials, c->red.counter, sD,
-        sS, c->d_scal + S_DIFF + 4);
+        sS, c->d_scal + S_DIFF + 4, 0.0, nullptr);
   else
     k_colsum<double><<<grid, kBlock, 0, c->stream>>>(
         (const double*)X, c->P.n, ld, 1, (const double*)Y, c->red.partials, c->red.counter, sD,
-        sS, c->d_scal + S_DIFF + 4);
+        sS, c->d_scal + S_DIFF + 4, 0.0, nullptr);
   HL_CHECK_LAUNCH(c);
 }
 

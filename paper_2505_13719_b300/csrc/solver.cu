@@ -170,7 +170,7 @@ struct Solver {
   // enqueue: pre-pass + fused operator at U (W and resid optional)
   void grad_enqueue(const void* U, void* W, void* resid) {
     if (P.C_J != 0.0 || P.has_trace) launch_colsum(c, U, ld, c->d_colsum, S_PRE);
-    launch_grad(c, U, ld, rank, pk, beta, c->d_colsum, GradOut{W, resid, nullptr});
+    launch_grad(c, U, ld, rank, pk, beta, GradOut{W, resid, nullptr});
     if (resid && P.has_trace) trace_fix(resid, nullptr, c->d_scal + S_PRE, -b_tr);
     R.grad_evals++;
   }
