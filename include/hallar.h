@@ -234,6 +234,161 @@ hallar_status hallar_grad_diag_noalloc(int64_t n, int32_t r, const int32_t* rowp
                                        double* g_out, void* stream, char* errbuf,
                                        int32_t errbuf_len);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of whole solves.  The paper solves one problem
+ * at a time (Section 5); this engine, which has no counterpart there, keeps a
+ * FIFO of solve requests and runs up to max_inflight of them at once, each in
+ * its own handle on its own CUDA stream driven by a worker thread, so their
+ * kernels overlap on the device.  A request is admitted when a worker is free
+ * and its estimated device footprint (hallar_solve_footprint) fits in what the
+ * HBM budget has left; requests that arrive while others run wait in the
+ * queue and are admitted as workers and memory free up.  Problem data, the
+ * factor and the multipliers stay on the device from admission to the end
+ * of the solve.  Every kernel is deterministic and handles share no device
+ * state, so a request's result does not depend on what else is in flight.
+ * ------------------------------------------------------------------------- */
+typedef struct hallar_server* hallar_server_t;
+
+typedef struct {
+  double hbm_budget_bytes;  /* summed footprint of the solves admitted at once (> 0) */
+  int32_t max_inflight;     /* solves on the device at once, 1..256                  */
+  int32_t device;           /* CUDA device of every solve                            */
+} hallar_server_options;
+
+/* One solve request: the arguments of hallar_create, the start factor and the
+ * options.  Every array is a HOST array; hallar_server_submit copies them, so
+ * the caller may release them when it returns.  U0 is n x r0, row-major,
+ * double for HALLAR_FP64 and float for HALLAR_MIXED (opt.precision); C_nnz is
+ * the length of C_col / C_val (C_rowptr[n]).  opt.stream is ignored. */
+typedef struct {
+  int64_t n, n1;
+  const int64_t* C_rowptr;
+  const int32_t* C_col;
+  const double* C_val;
+  int64_t C_nnz;
+  double C_J, C_I;
+  int32_t family;
+  int64_t m_pairs;
+  const int32_t* cons_i;
+  const int32_t* cons_j;
+  int32_t has_trace_row;
+  const double* b;
+  double tau2;
+  const void* U0;
+  int32_t r0;
+  hallar_options opt;
+} hallar_request;
+
+/* Aggregate counters of a server; latencies are from submit to completion. */
+typedef struct {
+  int64_t submitted, admitted, completed, failed, queued, inflight, max_inflight_seen;
+  double bytes_inflight, peak_bytes_inflight;
+  double p50_latency_s, p99_latency_s, mean_latency_s, max_latency_s;
+  double first_submit_to_last_done_s;
+} hallar_server_stats;
+
+/* Estimated device bytes of one solve of req (problem data, the solver's
+ * factors and vectors, the Lanczos basis, staging and reduction buffers, plus
+ * 5 % and 64 MB of allocator slack); host arithmetic only.  -1 if req is NULL. */
+int64_t hallar_solve_footprint(const hallar_request* req);
+
+/* Start a server (worker threads; no device memory until requests run).
+ * HALLAR_EINVAL for bad options, HALLAR_ECUDA if the device is unusable. */
+hallar_status hallar_server_create(const hallar_server_options* opt, hallar_server_t* out);
+
+/* Queue a solve.  *ticket (host) identifies it for hallar_server_wait.
+ * HALLAR_EINVAL for a NULL or malformed request (sizes, null arrays),
+ * HALLAR_ENOMEM when its footprint exceeds the whole budget.  Problems that
+ * only hallar_create detects (asymmetric C, bad indices) complete with that
+ * status. */
+hallar_status hallar_server_submit(hallar_server_t s, const hallar_request* req,
+                                   int64_t* ticket);
+
+/* Wait for a ticket.  timeout_s < 0 waits without limit.  When the call
+ * itself does not complete the ticket, *rank and *latency_s are set to -1:
+ * HALLAR_ETIMEOUT when the request is still queued or running at the
+ * timeout (the ticket stays valid), HALLAR_EINVAL for an unknown ticket or
+ * U_capacity below the rank.  A completed solve that hit its own time limit
+ * also returns HALLAR_ETIMEOUT, with its rank and latency (>= 0).  On
+ * completion the ticket is released and the call returns the solve's status:
+ *   res        (host, may be NULL) the hallar_result of the solve,
+ *   U          (host, may be NULL) n x *rank factor, leading dimension
+ *              U_capacity >= rank, in the request's precision,
+ *   p          (host, may be NULL) the m multipliers,
+ *   rank       (host, may be NULL) rank of U,
+ *   latency_s  (host, may be NULL) seconds from submit to completion. */
+hallar_status hallar_server_wait(hallar_server_t s, int64_t ticket, double timeout_s,
+                                 hallar_result* res, void* U, int32_t U_capacity, double* p,
+                                 int32_t* rank, double* latency_s);
+
+/* Counters (host).  Latency percentiles over every completed request. */
+hallar_status hallar_server_get_stats(hallar_server_t s, hallar_server_stats* st);
+
+/* Stop the server: queued requests are dropped, running solves finish, the
+ * workers exit and every result not yet waited for is released. */
+void hallar_server_destroy(hallar_server_t s);
+
+/* Message of the last failure of a server call ("" if none). */
+const char* hallar_server_last_error(hallar_server_t s);
+
+/* ---------------------------------------------------------------------------
+ * Batching: many uneven instances in one launch.  The paper evaluates one
+ * problem's operators at a time (Section 4); this layer, which has no
+ * counterpart there, stacks `count` instances into one segmented problem --
+ * instance k owns rows [row_off[k], row_off[k+1]) of a stacked factor and
+ * constraints [cons_off[k], cons_off[k+1]) -- and evaluates the fused
+ * constraint map + shift + SpMM of every instance in one launch of a
+ * grid-stride kernel sized to one wave of resident blocks, with per-instance
+ * penalties and per-instance reductions (summed per instance in a fixed
+ * order, so results are deterministic for a given kernel shape).  Supported
+ * instances: HALLAR_DIAG, HALLAR_EDGE and HALLAR_OBSERVED without the trace
+ * row and with C_J = 0 (Max-Cut and matrix completion); others return
+ * HALLAR_EINVAL.  The kernel shape (lanes per row, chunks per lane) for a
+ * factor width is chosen on the first call with that width: by timing the
+ * candidate shapes on the call's own data (autotune = 1; the choice is then
+ * fixed for the batch) or by the built-in rule (autotune = 0).
+ * ------------------------------------------------------------------------- */
+typedef struct hallar_batch* hallar_batch_t;
+
+/* Stack count >= 1 problems given as hallar_request (their U0, r0 and opt
+ * are ignored) in the precision `precision` on `stream` (NULL: a stream the
+ * batch creates).  Problem arrays are host arrays, copied.  HALLAR_EINVAL for
+ * an unsupported or invalid instance (hallar_batch_last_error(NULL) names
+ * it), HALLAR_ENOMEM, HALLAR_ECUDA. */
+hallar_status hallar_batch_create(int32_t count, const hallar_request* problems,
+                                  int32_t precision, int32_t autotune, void* stream,
+                                  hallar_batch_t* out);
+
+/* Layout (host pointers, any may be NULL): row_off[count+1], cons_off[count+1],
+ * the stacked order n_total and constraint count m_total. */
+hallar_status hallar_batch_layout(hallar_batch_t b, int64_t* row_off, int64_t* cons_off,
+                                  int64_t* n_total, int64_t* m_total);
+
+/* The fused operator of every instance in one launch (plus one per-instance
+ * reduction launch):
+ *   U     [n_total x r] stacked factors, row-major, leading dimension r, in
+ *         the batch precision (host or device),
+ *   p     [m_total] multipliers, beta [count] penalties (host or device),
+ *   W     [n_total x r] out: W_k = (C_k + A_k*(p'_k)) U_k (host or device),
+ *   g     [count] out: g_k = C_k.U_kU_k^T + p_k^T r_k + beta_k/2 |r_k|^2,
+ *   resid [m_total] out or NULL: r = A(UU^T) - b per constraint.
+ * 1 <= r <= 256.  Returns when the results are complete. */
+hallar_status hallar_batch_grad(hallar_batch_t b, const void* U, int32_t r, const double* p,
+                                const double* beta, void* W, double* g, double* resid);
+
+/* Kernel shape used for factor width r (host pointers): lanes per row G,
+ * 16-byte chunks per lane K, tuned = 1 when the autotuner timed it.
+ * HALLAR_EINVAL before the first hallar_batch_grad with that width. */
+hallar_status hallar_batch_shape(hallar_batch_t b, int32_t r, int32_t* G, int32_t* K,
+                                 int32_t* tuned);
+
+/* Free every resource of b (NULL is a no-op). */
+void hallar_batch_destroy(hallar_batch_t b);
+
+/* Message of the last failure on b; for b == NULL the last failure of
+ * hallar_batch_create on this thread. */
+const char* hallar_batch_last_error(hallar_batch_t b);
+
 /* Problem sizes of a handle (host pointers; any may be NULL). */
 hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz_merged,
                                int32_t* precision);

@@ -40,7 +40,31 @@ void dfree(Ctx* c, void* p) {
   if (!p) return;
   auto it = std::find(c->owned.begin(), c->owned.end(), p);
   if (it != c->owned.end()) c->owned.erase(it);
-  cudaFree(p);
+  cudaFreeAsync(p, c->stream);
+}
+
+namespace {
+std::mutex g_pin_mu;
+std::vector<double*> g_pin_free;
+constexpr int kPinSlab = 64;  // blocks per pinned slab
+}  // namespace
+
+double* pinned_scalars_acquire() {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  if (g_pin_free.empty()) {
+    double* slab = nullptr;
+    HL_CUDA(cudaMallocHost((void**)&slab, (size_t)kPinSlab * S_COUNT * sizeof(double)));
+    for (int i = kPinSlab - 1; i >= 0; --i) g_pin_free.push_back(slab + (size_t)i * S_COUNT);
+  }
+  double* p = g_pin_free.back();
+  g_pin_free.pop_back();
+  return p;
+}
+
+void pinned_scalars_release(double* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_pin_free.push_back(p);
 }
 
 void* ensure_buffer(Ctx* c, void** buf, size_t* cur, size_t bytes) {
@@ -114,7 +138,10 @@ bool is_device_ptr(const void* p) {
 template <class T>
 T* upload(Ctx* c, const T* host, size_t count) {
   T* d = dalloc<T>(c, count);
-  if (count) HL_CUDA(cudaMemcpy(d, host, count * sizeof(T), cudaMemcpyHostToDevice));
+  // from pageable memory the call returns once the data is staged, so the
+  // caller's array may be released afterwards
+  if (count)
+    HL_CUDA(cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   return d;
 }
 
@@ -124,12 +151,14 @@ bool finite_all(const double* a, size_t n) {
   return true;
 }
 
-// Validates the data and builds the merged CSR (layout in hallar_internal.cuh).
-void build_problem(Ctx* c, int64_t n, int64_t n1, const int64_t* rp, const int32_t* ci,
+}  // namespace
+
+// Validates the data and builds the merged CSR on the host (layout in
+// hallar_internal.cuh); throws Err on invalid input.
+void merge_problem(HostProblem& P, int64_t n, int64_t n1, const int64_t* rp, const int32_t* ci,
                    const double* cv, double C_J, double C_I, int family, int64_t m_pairs,
                    const int32_t* pi, const int32_t* pj, int has_trace, const double* b,
                    double tau2) {
-  Problem& P = c->P;
   if (n <= 0 || n >= (int64_t)INT32_MAX) fail(HALLAR_EINVAL, "n must be in [1, 2^31 - 1)");
   if (family < 0 || family > 2) fail(HALLAR_EINVAL, "unknown constraint family");
   if (!(tau2 > 0.0) || !std::isfinite(tau2)) fail(HALLAR_EINVAL, "tau2 must be positive and finite");
@@ -281,18 +310,44 @@ void build_problem(Ctx* c, int64_t n, int64_t n1, const int64_t* rp, const int32
     for (int64_t i = 0; i <= n; ++i) rowptr[i] = (int32_t)cnt[i];
   }
   P.nnz = (int64_t)col.size();
-  P.rowptr = upload(c, rowptr.data(), rowptr.size());
-  P.col = upload(c, col.data(), col.size());
-  if (!code.empty()) P.code = upload(c, code.data(), code.size());
-  if (!val.empty()) {
-    P.cval = upload(c, val.data(), val.size());
-    std::vector<float> v32(val.begin(), val.end());
+  P.rowptr = std::move(rowptr);
+  P.col = std::move(col);
+  P.code = std::move(code);
+  P.val = std::move(val);
+  P.cdiag = std::move(cdiag);
+  P.b.assign(b, b + m);
+}
+
+namespace {
+
+// device copies of a merged problem (float copies too for the mixed form)
+void upload_problem(Ctx* c, const HostProblem& H) {
+  Problem& P = c->P;
+  P.fam = H.fam;
+  P.api_family = H.api_family;
+  P.n = H.n;
+  P.n1 = H.n1;
+  P.m = H.m;
+  P.m_pairs = H.m_pairs;
+  P.nnz = H.nnz;
+  P.has_trace = H.has_trace;
+  P.C_J = H.C_J;
+  P.C_I = H.C_I;
+  P.tau2 = H.tau2;
+  P.b_norm1 = H.b_norm1;
+  P.c_norm1 = H.c_norm1;
+  P.rowptr = upload(c, H.rowptr.data(), H.rowptr.size());
+  P.col = upload(c, H.col.data(), H.col.size());
+  if (!H.code.empty()) P.code = upload(c, H.code.data(), H.code.size());
+  if (!H.val.empty()) {
+    P.cval = upload(c, H.val.data(), H.val.size());
+    std::vector<float> v32(H.val.begin(), H.val.end());
     P.cval32 = upload(c, v32.data(), v32.size());
   }
-  P.cdiag = upload(c, cdiag.data(), cdiag.size());
-  P.b = upload(c, b, (size_t)m);
+  P.cdiag = upload(c, H.cdiag.data(), H.cdiag.size());
+  P.b = upload(c, H.b.data(), H.b.size());
   if (c->opt.precision == HALLAR_MIXED) {
-    std::vector<float> cd32(cdiag.begin(), cdiag.end()), b32(b, b + m);
+    std::vector<float> cd32(H.cdiag.begin(), H.cdiag.end()), b32(H.b.begin(), H.b.end());
     P.cdiag32 = upload(c, cd32.data(), cd32.size());
     P.b32 = upload(c, b32.data(), b32.size());
   }
@@ -369,9 +424,10 @@ void release(Ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
-  for (void* p : c->owned) cudaFree(p);
+  for (void* p : c->owned) cudaFreeAsync(p, c->stream);
   c->owned.clear();
-  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  pinned_scalars_release(c->h_scal);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -447,15 +503,17 @@ hallar_status hallar_create(int64_t n, int64_t n1, const int64_t* C_rowptr, cons
     // 2 (ld + 1) column sums per block of the pre-pass (ld <= kColsumMax)
     c->red.partials = dalloc<double>(c, (size_t)kMaxBlocks * (2 * kColsumMax + 2));
     c->red.counter = dalloc<unsigned>(c, 16);
-    HL_CUDA(cudaMemset(c->red.counter, 0, 16 * sizeof(unsigned)));
+    HL_CUDA(cudaMemsetAsync(c->red.counter, 0, 16 * sizeof(unsigned), c->stream));
     c->d_scal = dalloc<double>(c, S_COUNT);
-    HL_CUDA(cudaMemset(c->d_scal, 0, S_COUNT * sizeof(double)));
-    HL_CUDA(cudaMallocHost((void**)&c->h_scal, S_COUNT * sizeof(double)));
+    HL_CUDA(cudaMemsetAsync(c->d_scal, 0, S_COUNT * sizeof(double), c->stream));
+    c->h_scal = pinned_scalars_acquire();
     c->d_colsum = dalloc<double>(c, 4 * kColsumMax);
-    HL_CUDA(cudaMemset(c->d_colsum, 0, 4 * kColsumMax * sizeof(double)));
-    build_problem(c, n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, m_pairs, cons_i, cons_j,
+    HL_CUDA(cudaMemsetAsync(c->d_colsum, 0, 4 * kColsumMax * sizeof(double), c->stream));
+    HostProblem hp;
+    merge_problem(hp, n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, m_pairs, cons_i, cons_j,
                   has_trace_row, b, tau2);
-    HL_CUDA(cudaDeviceSynchronize());
+    upload_problem(c, hp);
+    HL_CUDA(cudaStreamSynchronize(c->stream));
   } catch (const Err& e) {
     g_create_error = e.msg;
     release(c);
@@ -539,8 +597,11 @@ hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
     double pr = hsc[S_GRAD + 1], rr = hsc[S_GRAD + 2];
     if (c->P.has_trace) {
       double pt = 0.0, bt = 0.0;
-      HL_CUDA(cudaMemcpy(&pt, pd + (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
-      HL_CUDA(cudaMemcpy(&bt, c->P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
+      HL_CUDA(cudaMemcpyAsync(&pt, pd + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+      HL_CUDA(cudaMemcpyAsync(&bt, c->P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+      HL_CUDA(cudaStreamSynchronize(c->stream));
       const double rt = hsc[S_PRE] - bt;
       pr += pt * rt;
       rr += rt * rt;

@@ -45,6 +45,24 @@ struct Problem {
   float* b32 = nullptr;
 };
 
+// the merged problem on the host, before upload (also the building block of
+// a batch: one per stacked instance)
+struct HostProblem {
+  int fam = FAM_DIAG;
+  int api_family = 0;
+  int64_t n = 0, n1 = 0, m = 0, m_pairs = 0, nnz = 0;
+  int has_trace = 0;
+  double C_J = 0.0, C_I = 0.0, tau2 = 1.0;
+  double b_norm1 = 0.0, c_norm1 = 0.0;
+  std::vector<int32_t> rowptr, col, code;
+  std::vector<double> val, cdiag, b;
+};
+// validate and merge (throws Err); see hallar_create for the arguments
+void merge_problem(HostProblem& P, int64_t n, int64_t n1, const int64_t* rp, const int32_t* ci,
+                   const double* cv, double C_J, double C_I, int family, int64_t m_pairs,
+                   const int32_t* pi, const int32_t* pj, int has_trace, const double* b,
+                   double tau2);
+
 // ---------------------------------------------------------------------------
 // reductions: per-block partials, summed by the last block in a fixed order
 // ---------------------------------------------------------------------------
@@ -146,14 +164,22 @@ struct Err {
 inline void fail(hallar_status st, const std::string& m) { throw Err{st, m}; }
 
 // buffers -------------------------------------------------------------------
+// Device buffers are stream-ordered allocations on the handle's stream
+// (cudaMallocAsync / cudaFreeAsync): unlike cudaFree, releasing them does not
+// synchronise the device, so handles on different streams -- the serving
+// engine's concurrent solves -- never wait for one another's work.
 template <class T>
 T* dalloc(Ctx* c, size_t count) {
   void* p = nullptr;
   if (count == 0) count = 1;
-  HL_CUDA(cudaMalloc(&p, count * sizeof(T)));
+  HL_CUDA(cudaMallocAsync(&p, count * sizeof(T), c->stream));
   c->owned.push_back(p);
   return static_cast<T*>(p);
 }
+// pinned blocks of S_COUNT doubles for the scalar read-backs, recycled across
+// handles (cudaFreeHost would synchronise the device)
+double* pinned_scalars_acquire();
+void pinned_scalars_release(double* p);
 void dfree(Ctx* c, void* p);
 // grow *buf to at least `bytes` (contents not kept)
 void* ensure_buffer(Ctx* c, void** buf, size_t* cur_bytes, size_t bytes);

@@ -142,7 +142,11 @@ struct Solver {
     vprev = salloc<double>(n);
     v0 = salloc<double>(n);
     gram = salloc<double>((size_t)ld_max * ld_max);
-    if (P.has_trace) HL_CUDA(cudaMemcpy(&b_tr, P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost));
+    if (P.has_trace) {
+      HL_CUDA(cudaMemcpyAsync(&b_tr, P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+      HL_CUDA(cudaStreamSynchronize(c->stream));
+    }
   }
 
   void copyf(void* dst, const void* src) {

@@ -26,7 +26,11 @@ FAMILY = {"diag": HALLAR_DIAG, "edge": HALLAR_EDGE, "observed": HALLAR_OBSERVED}
 EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_grad",
             "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
             "hallar_destroy", "hallar_last_error", "hallar_status_string", "hallar_profile",
-            "hallar_grad_diag_noalloc")
+            "hallar_grad_diag_noalloc", "hallar_solve_footprint", "hallar_server_create",
+            "hallar_server_submit", "hallar_server_wait", "hallar_server_get_stats",
+            "hallar_server_destroy", "hallar_server_last_error", "hallar_batch_create",
+            "hallar_batch_layout", "hallar_batch_grad", "hallar_batch_shape",
+            "hallar_batch_destroy", "hallar_batch_last_error")
 
 
 class hallar_options(C.Structure):
@@ -56,6 +60,32 @@ class hallar_result(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class hallar_server_options(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_double), ("max_inflight", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class hallar_request(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n1", C.c_int64), ("C_rowptr", C.c_void_p),
+                ("C_col", C.c_void_p), ("C_val", C.c_void_p), ("C_nnz", C.c_int64),
+                ("C_J", C.c_double), ("C_I", C.c_double), ("family", C.c_int32),
+                ("m_pairs", C.c_int64), ("cons_i", C.c_void_p), ("cons_j", C.c_void_p),
+                ("has_trace_row", C.c_int32), ("b", C.c_void_p), ("tau2", C.c_double),
+                ("U0", C.c_void_p), ("r0", C.c_int32), ("opt", hallar_options)]
+
+
+class hallar_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("failed", C.c_int64), ("queued", C.c_int64), ("inflight", C.c_int64),
+                ("max_inflight_seen", C.c_int64), ("bytes_inflight", C.c_double),
+                ("peak_bytes_inflight", C.c_double), ("p50_latency_s", C.c_double),
+                ("p99_latency_s", C.c_double), ("mean_latency_s", C.c_double),
+                ("max_latency_s", C.c_double), ("first_submit_to_last_done_s", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libhallar.so not built ({LIB_PATH}); run "
@@ -75,6 +105,19 @@ def _load():
         "hallar_profile": ([P, I32, P, P, P], C.c_int),
         "hallar_grad_diag_noalloc": ([I64, I32, P, P, P, P, P, P, D, P, P, P, P, P, C.c_char_p,
                                       I32], C.c_int),
+        "hallar_solve_footprint": ([P], I64),
+        "hallar_server_create": ([P, C.POINTER(C.c_void_p)], C.c_int),
+        "hallar_server_submit": ([P, P, C.POINTER(I64)], C.c_int),
+        "hallar_server_wait": ([P, I64, D, P, P, I32, P, P, P], C.c_int),
+        "hallar_server_get_stats": ([P, P], C.c_int),
+        "hallar_server_destroy": ([P], None),
+        "hallar_server_last_error": ([P], C.c_char_p),
+        "hallar_batch_create": ([I32, P, I32, I32, P, C.POINTER(C.c_void_p)], C.c_int),
+        "hallar_batch_layout": ([P, P, P, P, P], C.c_int),
+        "hallar_batch_grad": ([P, P, I32, P, P, P, P, P], C.c_int),
+        "hallar_batch_shape": ([P, I32, P, P, P], C.c_int),
+        "hallar_batch_destroy": ([P], None),
+        "hallar_batch_last_error": ([P], C.c_char_p),
         "hallar_destroy": ([P], None),
         "hallar_last_error": ([P], C.c_char_p),
         "hallar_status_string": ([C.c_int], C.c_char_p),
@@ -261,3 +304,193 @@ def create_from_instance(inst, precision=HALLAR_FP64, **options) -> Handle:
                       inst.C_I, inst.family, inst.cons_i, inst.cons_j, inst.has_trace_row,
                       inst.b, inst.tau2, opt)
     return Handle(h=h, n=inst.n, m=inst.m, precision=precision)
+
+
+# ---------------------------------------------------------------------------
+# serving engine
+# ---------------------------------------------------------------------------
+def request_from_instance(inst, U0, precision=HALLAR_FP64, **options):
+    """A hallar_request for an instances.Instance and a host start factor.
+    Returns (request, keep): `keep` holds the arrays the request points to;
+    it must stay alive until hallar_server_submit returns."""
+    opt = hallar_default_options(precision=precision, **options)
+    fam = FAMILY[inst.family] if isinstance(inst.family, str) else int(inst.family)
+    dt = np.float32 if precision == HALLAR_MIXED else np.float64
+    keep = {
+        "rp": None if inst.C_rowptr is None else np.ascontiguousarray(inst.C_rowptr, np.int64),
+        "ci": np.ascontiguousarray([] if inst.C_col is None else inst.C_col, np.int32),
+        "cv": np.ascontiguousarray([] if inst.C_val is None else inst.C_val, np.float64),
+        "pi": np.ascontiguousarray(inst.cons_i, np.int32),
+        "pj": np.ascontiguousarray(inst.cons_j, np.int32),
+        "b": np.ascontiguousarray(inst.b, np.float64),
+        "U0": np.ascontiguousarray(U0, dt),
+    }
+    q = hallar_request()
+    q.n, q.n1 = int(inst.n), int(inst.n1)
+    q.C_rowptr = _ptr(keep["rp"])
+    q.C_col, q.C_val = _ptr(keep["ci"]), _ptr(keep["cv"])
+    q.C_nnz = 0 if keep["rp"] is None else int(keep["rp"][-1])
+    q.C_J, q.C_I = float(inst.C_J), float(inst.C_I)
+    q.family = fam
+    q.m_pairs = 0 if fam == HALLAR_DIAG else int(keep["pi"].shape[0])
+    q.cons_i, q.cons_j = _ptr(keep["pi"]), _ptr(keep["pj"])
+    q.has_trace_row = int(bool(inst.has_trace_row))
+    q.b = _ptr(keep["b"])
+    q.tau2 = float(inst.tau2)
+    q.U0 = _ptr(keep["U0"])
+    q.r0 = int(keep["U0"].shape[1])
+    q.opt = opt
+    return q, keep
+
+
+def hallar_solve_footprint(req) -> int:
+    return int(_lib.hallar_solve_footprint(C.byref(req)))
+
+
+def _scheck(status, s, allow=()):
+    if status != HALLAR_OK and status not in allow:
+        raise HallarError(status, _lib.hallar_server_last_error(s).decode())
+    return status
+
+
+def hallar_server_create(hbm_budget_bytes, max_inflight, device=0):
+    o = hallar_server_options(float(hbm_budget_bytes), int(max_inflight), int(device))
+    s = C.c_void_p()
+    st = _lib.hallar_server_create(C.byref(o), C.byref(s))
+    if st != HALLAR_OK:
+        raise HallarError(st, "hallar_server_create failed")
+    return s
+
+
+def hallar_server_submit(s, req) -> int:
+    t = C.c_int64()
+    _scheck(_lib.hallar_server_submit(s, C.byref(req), C.byref(t)), s)
+    return t.value
+
+
+def hallar_server_wait(s, ticket, timeout_s=-1.0, U=None, U_capacity=0, p=None):
+    """Returns (status, hallar_result, rank, latency_s); U / p filled when given."""
+    res = hallar_result()
+    rank = C.c_int32()
+    lat = C.c_double()
+    st = _lib.hallar_server_wait(s, int(ticket), float(timeout_s), C.byref(res), _ptr(U),
+                                 int(U_capacity), _ptr(p), C.byref(rank), C.byref(lat))
+    if lat.value < 0.0 and st != HALLAR_ETIMEOUT:
+        _scheck(st, s)  # the call itself failed (unknown ticket, capacity)
+    return st, res, rank.value, lat.value
+
+
+def hallar_server_get_stats(s) -> dict:
+    st = hallar_server_stats()
+    _scheck(_lib.hallar_server_get_stats(s, C.byref(st)), s)
+    return st.as_dict()
+
+
+def hallar_server_destroy(s):
+    _lib.hallar_server_destroy(s)
+
+
+def hallar_server_last_error(s) -> str:
+    return _lib.hallar_server_last_error(s).decode()
+
+
+class Server:
+    """hallar_server_* wrapper: submit instances, wait for solutions."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight, device=0):
+        self.s = hallar_server_create(hbm_budget_bytes, max_inflight, device)
+        self.meta = {}
+
+    def submit(self, inst, U0, precision=HALLAR_FP64, **options) -> int:
+        q, keep = request_from_instance(inst, U0, precision, **options)
+        t = hallar_server_submit(self.s, q)
+        del keep
+        self.meta[t] = (inst.n, inst.m, precision, int(options.get("r_cap", 32)))
+        return t
+
+    def wait(self, ticket, timeout_s=-1.0):
+        """(status, result, U [n x rank], p [m], latency_s) of a ticket."""
+        n, m, precision, r_cap = self.meta[ticket]
+        dt = np.float32 if precision == HALLAR_MIXED else np.float64
+        cap = r_cap + 1
+        U = np.empty((n, cap), dtype=dt)
+        p = np.empty(m)
+        st, res, rank, lat = hallar_server_wait(self.s, ticket, timeout_s, U, cap, p)
+        if st == HALLAR_ETIMEOUT and lat < 0.0:  # still queued or running
+            return st, None, None, None, None
+        del self.meta[ticket]
+        return st, res, np.ascontiguousarray(U[:, :rank]), p, lat
+
+    def stats(self) -> dict:
+        return hallar_server_get_stats(self.s)
+
+    def close(self):
+        if self.s is not None:
+            hallar_server_destroy(self.s)
+            self.s = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---------------------------------------------------------------------------
+# batched operators over a segmented CSR
+# ---------------------------------------------------------------------------
+def _bcheck(status, b):
+    if status != HALLAR_OK:
+        raise HallarError(status, _lib.hallar_batch_last_error(b).decode())
+    return status
+
+
+class Batch:
+    """hallar_batch_*: many instances stacked into one segmented problem."""
+
+    def __init__(self, instances, precision=HALLAR_FP64, autotune=False, stream=None):
+        reqs, keep = [], []
+        for inst in instances:
+            q, k = request_from_instance(inst, np.zeros((inst.n, 1)), precision)
+            reqs.append(q)
+            keep.append(k)
+        arr = (hallar_request * len(reqs))(*reqs)
+        self.b = C.c_void_p()
+        _bcheck(_lib.hallar_batch_create(len(reqs), arr, int(precision), int(bool(autotune)),
+                                         stream, C.byref(self.b)), None)
+        del keep
+        self.count = len(reqs)
+        self.precision = precision
+        self.row_off = np.empty(self.count + 1, np.int64)
+        self.cons_off = np.empty(self.count + 1, np.int64)
+        nt, mt = C.c_int64(), C.c_int64()
+        _bcheck(_lib.hallar_batch_layout(self.b, _ptr(self.row_off), _ptr(self.cons_off),
+                                         C.byref(nt), C.byref(mt)), self.b)
+        self.n_total, self.m_total = nt.value, mt.value
+
+    def grad(self, U, r, p, beta, W, g, resid=None):
+        return _bcheck(_lib.hallar_batch_grad(self.b, _ptr(U), int(r), _ptr(p), _ptr(beta),
+                                              _ptr(W), _ptr(g), _ptr(resid)), self.b)
+
+    def shape(self, r):
+        G, K, t = C.c_int32(), C.c_int32(), C.c_int32()
+        _bcheck(_lib.hallar_batch_shape(self.b, int(r), C.byref(G), C.byref(K), C.byref(t)),
+                self.b)
+        return G.value, K.value, bool(t.value)
+
+    def close(self):
+        if self.b is not None:
+            _lib.hallar_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

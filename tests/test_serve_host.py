@@ -1,0 +1,45 @@
+"""Host-side parts of the serving engine that need no GPU: the footprint
+estimate that admission charges, and option validation."""
+import pytest
+
+from paper_2505_13719_b300 import instances as I
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2505_13719_b300.build import build_library
+    build_library()
+    from paper_2505_13719_b300 import hallar
+    return hallar
+
+
+def footprint(H, inst, prec=0, **opts):
+    q, keep = H.request_from_instance(inst, I.initial_factor(inst.n, 2, 1), prec, **opts)
+    return H.hallar_solve_footprint(q)
+
+
+def test_footprint_covers_the_dominant_buffers(H):
+    inst = I.maxcut_torus(100, "unit")  # n = 1e4
+    n = inst.n
+    fp = footprint(H, inst, 0, r_cap=32, lanczos_kmax=300)
+    # at least the Lanczos basis (n x 300 doubles) and ten factor buffers
+    # (n x 34 doubles each: r_cap + 1 padded to an even width)
+    assert fp >= n * 300 * 8 + 10 * n * 34 * 8
+    # and not absurdly more (allocator slack is 5 % + 64 MB)
+    assert fp <= 2 * (n * 300 * 8 + 10 * n * 34 * 8) + (80 << 20)
+
+
+def test_footprint_grows_with_size_rank_and_precision(H):
+    small, big = I.maxcut_torus(50, "unit"), I.maxcut_torus(100, "unit")
+    assert footprint(H, big) > footprint(H, small)
+    assert footprint(H, big, r_cap=64) > footprint(H, big, r_cap=8)
+    assert footprint(H, big, 0) > footprint(H, big, 1)  # float factors are half the size
+
+
+def test_server_options_are_validated(H):
+    with pytest.raises(H.HallarError) as e:
+        H.hallar_server_create(0.0, 2)
+    assert e.value.status == H.HALLAR_EINVAL
+    with pytest.raises(H.HallarError) as e:
+        H.hallar_server_create(1e9, 0)
+    assert e.value.status == H.HALLAR_EINVAL
