@@ -73,6 +73,29 @@ struct OpX : OpBase {
   }
 };
 
+// step 3's x update and, in the same pass, step 2's x~ of the next
+// iteration's first trial (whose stepsize L is the accepted one, so its
+// weights are known): x <- cy y + cx x + cxt xt, then xt <- wy y + wx x,
+// with the same arithmetic as OpX followed by OpXt
+template <class T>
+struct OpXXt : OpBase {
+  T* x; T* xt; const T* y; T cy, cx, cxt, wy, wx;
+  __device__ void operator()(int64_t v, Acc<T>*) const {
+    constexpr int VEC = V16<T>::N;
+    T a[VEC], b[VEC], t[VEC], o[VEC], q[VEC];
+    HL_LOAD(y, v, a);
+    HL_LOAD(x, v, b);
+    HL_LOAD(xt, v, t);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+      o[k] = tfma(cy, a[k], tfma(cx, b[k], cxt * t[k]));
+      q[k] = tfma(wy, a[k], wx * o[k]);
+    }
+    store_chunk<T>(x, v * VEC, o);
+    store_chunk<T>(xt, v * VEC, q);
+  }
+};
+
 // z = xt - grad psi_s(xt) / L with grad psi_s = 2 lam W + xt - center;
 // red[0] = |z|^2 (the ball projection is the scaling min(1, tau/|z|))
 template <class T>
@@ -364,6 +387,17 @@ void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, d
   const double cxt = -a * (L - mu) / tk_new;
   HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpX<T>{{}, (T*)x, (const T*)y, (const T*)xt, (T)cy, (T)cx,
                                                (T)cxt}, -1));
+}
+
+void launch_fista_x_xt(Ctx* c, void* x, const void* y, void* xt, double mu, double a,
+                       double tk, double tk_new, double L, double A_next, double a_next, int ld) {
+  const int64_t ne = c->P.n * (int64_t)ld;
+  const double cy = (mu * a + a * (L - mu)) / tk_new;
+  const double cx = tk / tk_new;
+  const double cxt = -a * (L - mu) / tk_new;
+  const double wy = A_next / (A_next + a_next), wx = a_next / (A_next + a_next);
+  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXXt<T>{{}, (T*)x, (T*)xt, (const T*)y, (T)cy, (T)cx,
+                                                 (T)cxt, (T)wy, (T)wx}, -1));
 }
 
 void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,

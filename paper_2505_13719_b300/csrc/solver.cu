@@ -222,6 +222,12 @@ struct Solver {
     if (el > o.time_limit_s) throw Err{HALLAR_ETIMEOUT, "time limit reached"};
   }
 
+  // step 2's a_j for the trial stepsize Ln (the positive root of
+  // (Ln - mu) a^2 = tk (A + a))
+  static double next_a(double tk, double A, double Ln, double mu) {
+    return (tk + std::sqrt(tk * tk + 4.0 * tk * A * (Ln - mu))) / (2.0 * (Ln - mu));
+  }
+
   // ADAP-FISTA on psi_s = lam g + 1/2 |. - ctr|^2 from x0 = ctr.
   // On success ynew holds y, z its unprojected step and *Lout the final L.
   bool fista(double lamv, double mu, double L0, double* Lout) {
@@ -229,13 +235,15 @@ struct Solver {
     copyf(y, ctr);
     double A = 0.0, tk = 1.0, L = L0;
     const double tauv = tau();
+    bool xt_ready = false;  // x~ of the first trial already formed by step 3's pass
     for (int it = 0; it < o.max_fista; ++it) {
       R.fista_iters++;
       if ((it & 15) == 15) check_time();
       double Ln = L, a = 0.0, d2 = 0.0, dy0 = 0.0;
       for (;;) {                                                 // step 2
-        a = (tk + std::sqrt(tk * tk + 4.0 * tk * A * (Ln - mu))) / (2.0 * (Ln - mu));
-        if (A == 0.0) copyf(xt, x);
+        a = next_a(tk, A, Ln, mu);
+        if (xt_ready) xt_ready = false;
+        else if (A == 0.0) copyf(xt, x);
         else launch_fista_xt(c, xt, y, x, A, a, ld);
         grad_enqueue(xt, Wg, rX);
         launch_fista_z(c, z, xt, Wg, ctr, lamv, Ln, ld);
@@ -263,14 +271,20 @@ struct Solver {
         }
       }
       const double A_new = A + a, tk_new = tk + a * mu;            // step 3
-      launch_fista_x(c, x, ynew, xt, mu, a, tk, tk_new, Ln, ld);
       const double snorm = (Ln - mu) * std::sqrt(d2);
       *Lout = Ln;
+      // steps 4 and 5 read only scalars of this trial, and x_{j+1} serves
+      // only later iterations: an iteration that returns skips its update
       if (dy0 < o.chi * A_new * Ln * d2) {                          // step 4
         R.fista_failures++;
         return false;
       }
       if (snorm <= o.sigma * std::sqrt(dy0)) return true;           // step 5
+      // step 3's x update; the next iteration's first trial keeps L = Ln,
+      // so its x~ comes out of the same pass
+      launch_fista_x_xt(c, x, ynew, xt, mu, a, tk, tk_new, Ln, A_new,
+                        next_a(tk_new, A_new, Ln, mu), ld);
+      xt_ready = true;
       std::swap(y, ynew);
       A = A_new;
       tk = tk_new;
