@@ -161,8 +161,10 @@ hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
                           double beta, void* W, double* g_val, double* resid);
 
 /* Minimum eigenpair of G = C + A*(p') (Alg. 1 step 7, eq. Grad X Space) by
- * Lanczos with full reorthogonalisation, restarted from the Ritz vector
- * every kmax steps, until ||G v - lambda v|| <= tol or 50 restarts.
+ * Lanczos in FP64 with partial reorthogonalisation (the basis is swept
+ * against when Simon's estimate of the loss of orthogonality passes
+ * sqrt(eps)), restarted from the Ritz vector every kmax steps, until
+ * ||G v - lambda v|| <= tol or 50 restarts.
  *   pshift [m]  p' (doubles).
  *   v0     [n]  start vector, or NULL for the SplitMix64 vector of opt.seed.
  *   lambda_min (host), v [n] (unit), iters (host), resid (host): outputs;

@@ -242,11 +242,10 @@ void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst,
                      double scale_src);
 void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, double a,
                      int ld);
-// launch_fista_x followed by launch_fista_xt(xt, y, x, A_next, a_next) in one pass
+// ADAP-FISTA step 3's x update, x <- [mu a y + tk x - a (L - mu)(xt - y)] / tk_new,
+// and in the same pass the next first trial's x~ = (A_next y + a_next x) / (A_next + a_next)
 void launch_fista_x_xt(Ctx* c, void* x, const void* y, void* xt, double mu, double a,
                        double tk, double tk_new, double L, double A_next, double a_next, int ld);
-void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, double a,
-                    double tk, double tk_new, double L, int ld);
 void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,
                     double lam, double L, int ld);
 void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* center,

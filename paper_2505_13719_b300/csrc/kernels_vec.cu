@@ -57,22 +57,6 @@ struct OpXt : OpBase {
   }
 };
 
-// x <- (mu a y + tk x - a s) / tk_new, s = (L - mu)(xt - y)   (step 3)
-template <class T>
-struct OpX : OpBase {
-  T* x; const T* y; const T* xt; T cy, cx, cxt;
-  __device__ void operator()(int64_t v, Acc<T>*) const {
-    constexpr int VEC = V16<T>::N;
-    T a[VEC], b[VEC], t[VEC], o[VEC];
-    HL_LOAD(y, v, a);
-    HL_LOAD(x, v, b);
-    HL_LOAD(xt, v, t);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) o[k] = tfma(cy, a[k], tfma(cx, b[k], cxt * t[k]));
-    store_chunk<T>(x, v * VEC, o);
-  }
-};
-
 // step 3's x update and, in the same pass, step 2's x~ of the next
 // iteration's first trial (whose stepsize L is the accepted one, so its
 // weights are known): x <- cy y + cx x + cxt xt, then xt <- wy y + wx x,
@@ -376,17 +360,6 @@ void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, d
   const double wy = A / (A + a), wx = a / (A + a);
   HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXt<T>{{}, (T*)xt, (const T*)y, (const T*)x, (T)wy, (T)wx},
                                  -1));
-}
-
-void launch_fista_x(Ctx* c, void* x, const void* y, const void* xt, double mu, double a,
-                    double tk, double tk_new, double L, int ld) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  // x_new = [mu a y + tk x - a (L - mu)(xt - y)] / tk_new
-  const double cy = (mu * a + a * (L - mu)) / tk_new;
-  const double cx = tk / tk_new;
-  const double cxt = -a * (L - mu) / tk_new;
-  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpX<T>{{}, (T*)x, (const T*)y, (const T*)xt, (T)cy, (T)cx,
-                                               (T)cxt}, -1));
 }
 
 void launch_fista_x_xt(Ctx* c, void* x, const void* y, void* xt, double mu, double a,
