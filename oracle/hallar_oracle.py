@@ -27,9 +27,9 @@ adjoint identity, finite differences and the Max-Cut cut identity; Lanczos
 against dense eigendecomposition and the closed-form torus and hypercube
 spectra; the Frank-Wolfe step as an exact line search; ADAP-AIPP's output
 invariants; full solves against closed-form SDP values with a dense dual
-certificate.  Parity unpinned: iteration counts and trajectories (they follow
-the readings, not the paper), and ``splitmix64_uniform`` beyond range and
-determinism (it only draws Lanczos start vectors; no result depends on it).
+certificate; ``splitmix64_uniform`` against the generator's published output
+words from state 0.  Parity unpinned: iteration counts and trajectories (they
+follow the readings, not the paper).
 """
 from __future__ import annotations
 

@@ -57,6 +57,16 @@ def test_lanczos_hypercube_closed_form(d):
     assert abs(er.lam - (c - d / 2.0)) <= 1e-9
 
 
+def test_splitmix_matches_the_published_output_words():
+    # SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) from state 0 produces
+    # the 64-bit words e220a8397b1dcdaf, 6e789e6aa1b965f4, 06c45d188009454f
+    # (the reference sequence of the published generator); the oracle's
+    # values are 2 (w >> 11) 2^-53 - 1 of those words
+    words = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    want = np.array([2.0 * (w >> 11) / 2.0 ** 53 - 1.0 for w in words])
+    assert np.array_equal(O.splitmix64_uniform(0, 3), want)
+
+
 def test_splitmix_uniform_range_and_determinism():
     a = O.splitmix64_uniform(42, 100000)
     b = O.splitmix64_uniform(42, 100000)
