@@ -330,7 +330,8 @@ hallar_status hallar_server_get_stats(hallar_server_t s, hallar_server_stats* st
  * workers exit and every result not yet waited for is released. */
 void hallar_server_destroy(hallar_server_t s);
 
-/* Message of the last failure of a server call ("" if none). */
+/* Message of the last failure of a server call ("" if none), copied for the
+ * calling thread: valid until that thread's next call of this function. */
 const char* hallar_server_last_error(hallar_server_t s);
 
 /* ---------------------------------------------------------------------------

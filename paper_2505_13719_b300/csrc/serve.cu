@@ -387,9 +387,13 @@ void hallar_server_destroy(hallar_server_t s) {
 }
 
 const char* hallar_server_last_error(hallar_server_t s) {
+  // a copy per calling thread: the server's own string may change as soon as
+  // the lock is released (workers and other callers write it)
+  static thread_local std::string copy;
   if (!s) return "";
   std::lock_guard<std::mutex> lk(s->mu);
-  return s->last_error.c_str();
+  copy = s->last_error;
+  return copy.c_str();
 }
 
 }  // extern "C"
