@@ -327,7 +327,8 @@ hallar_status hallar_server_wait(hallar_server_t s, int64_t ticket, double timeo
 hallar_status hallar_server_get_stats(hallar_server_t s, hallar_server_stats* st);
 
 /* Stop the server: queued requests are dropped, running solves finish, the
- * workers exit and every result not yet waited for is released. */
+ * workers exit and every result not yet waited for is released.  No other
+ * call on s may run concurrently with this one or follow it. */
 void hallar_server_destroy(hallar_server_t s);
 
 /* Message of the last failure of a server call ("" if none), copied for the
