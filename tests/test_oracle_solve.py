@@ -143,3 +143,51 @@ def test_rank_trim_keeps_leading_subspace():
     X, Xt = Y @ Y.T, Yt @ Yt.T
     assert Yt.shape == (30, 4)
     assert np.linalg.norm(X - Xt) <= 1e-2 * np.linalg.norm(X)
+
+
+def test_kkt_measures_at_a_closed_form_optimum():
+    # For a bipartite graph with unit weights and C = -L/4 an exact optimal
+    # pair is known: X = v v^T with v the +-1 two-colouring (v_i v_j = -1 on
+    # every edge, so C.X = -|E|) and multipliers p_i = deg_i / 2, for which
+    # S = C + Diag(p) = (D + A)/4 is the signless Laplacian over 4, psd with
+    # v itself as null vector ((A v)_i = -deg_i v_i), and -b^T p = -|E|.
+    N = 6
+    inst = I.maxcut_torus(N, "unit")
+    n = inst.n
+    ei, ej = I.torus_graph(N, N)
+    colour = np.full(n, -1)
+    colour[0] = 0
+    adj = [[] for _ in range(n)]
+    for a, b in zip(ei, ej):
+        adj[a].append(b)
+        adj[b].append(a)
+    stack = [0]
+    while stack:
+        i = stack.pop()
+        for j in adj[i]:
+            if colour[j] < 0:
+                colour[j] = 1 - colour[i]
+                stack.append(j)
+    assert all(colour[a] != colour[b] for a, b in zip(ei, ej))  # bipartite
+    v = np.where(colour == 0, 1.0, -1.0)
+    U = v[:, None]
+    deg = np.bincount(np.concatenate([ei, ej]), minlength=n).astype(float)
+    p = deg / 2.0
+    E = float(len(ei))
+    S = dense_C(inst) + np.diag(p)
+    lam = float(np.linalg.eigvalsh(S)[0])
+    assert abs(lam) <= 1e-12
+    cn = O.c_norm1(inst)
+    assert cn == pytest.approx(2.0)  # |C_ii| + sum_j |C_ij| = 1 + 4 / 4
+    pval, dval, rp, rg, rd = O.kkt_measures(inst, U, p, 0.0, lam, cn)
+    assert pval == pytest.approx(-E, rel=1e-15) and dval == pytest.approx(-E, rel=1e-15)
+    assert rp == 0.0 and rg <= 1e-15 and rd <= 1e-12
+    # moving p up keeps S psd but opens a duality gap of 0.1 n
+    pval, dval, rp, rg, rd = O.kkt_measures(inst, U, p + 0.1, 0.0, lam + 0.1, cn)
+    assert rg == pytest.approx(0.1 * n / (1 + 2 * E + 0.1 * n), rel=1e-12) and rd == 0.0
+    # moving p down makes S indefinite by 0.1: dual infeasibility 0.1 / (1 + |C|_1)
+    pval, dval, rp, rg, rd = O.kkt_measures(inst, U, p - 0.1, 0.0, lam - 0.1, cn)
+    assert rd == pytest.approx(0.1 / (1 + cn), rel=1e-10)
+    # shrinking U breaks diag(X) = 1 by 0.19 on every row
+    pval, dval, rp, rg, rd = O.kkt_measures(inst, 0.9 * U, p, 0.0, lam, cn)
+    assert rp == pytest.approx(0.19 * math.sqrt(n) / (1 + n), rel=1e-12)
