@@ -191,3 +191,33 @@ def test_kkt_measures_at_a_closed_form_optimum():
     # shrinking U breaks diag(X) = 1 by 0.19 on every row
     pval, dval, rp, rg, rd = O.kkt_measures(inst, 0.9 * U, p, 0.0, lam, cn)
     assert rp == pytest.approx(0.19 * math.sqrt(n) / (1 + n), rel=1e-12)
+
+
+def test_adap_fista_on_a_quadratic_with_a_closed_form_prox():
+    # p = 0 and beta = 0 leave g(U) = C.UU^T; with C = c I (no edges, C_I = c)
+    # psi(U) = lam c |U|^2 + 1/2 |U - U0|^2 has the minimiser U0 / (1 + 2 lam c)
+    # and Hessian H = 1 + 2 lam c.  ADAP-FISTA (Appendix A.1) started at U0
+    # must stop at step 5 with |(L - mu)(x~ - y)| <= sigma |y - U0|; the
+    # step-2 test forces L >= 2 H / (1 - chi), which bounds |y - U*| by
+    # sigma |y - U0|.  With the ball inactive, V = grad psi(y) exactly.
+    n, r, c, lam = 50, 3, 0.5, 0.7
+    inst = I.maxcut(n, np.zeros(0, int), np.zeros(0, int))
+    inst.C_I = c
+    rng = np.random.default_rng(21)
+    U0 = 0.3 * rng.standard_normal((n, r))
+    opt = O.Options()
+    sub = O._Subproblem(inst, np.zeros(n), 0.0, O.Counters())
+    status, y, L, V, dg = O.adap_fista(sub, lam, U0, 0.5, 1.0, opt, math.sqrt(inst.tau2))
+    assert status == "success"
+    H = 1.0 + 2.0 * lam * c
+    Ustar = U0 / H
+    assert L >= 2.0 * H / (1.0 - opt.chi)
+    assert np.linalg.norm(y - Ustar) <= opt.sigma * np.linalg.norm(y - U0)
+    grad_psi = H * y - U0
+    assert np.linalg.norm(V - grad_psi) <= 1e-12 * np.linalg.norm(U0)
+    dg0 = dg[0]
+    assert dg0 == pytest.approx(c * (np.sum(y * y) - np.sum(U0 * U0)), rel=1e-12)
+
+    def psi(U):
+        return lam * c * float(np.sum(U * U)) + 0.5 * float(np.sum((U - U0) ** 2))
+    assert psi(y) < psi(U0)
