@@ -393,6 +393,20 @@ void hallar_batch_destroy(hallar_batch_t b);
  * hallar_batch_create on this thread. */
 const char* hallar_batch_last_error(hallar_batch_t b);
 
+/* Validate a problem exactly as hallar_create does and build its merged CSR
+ * on the host, without touching a device (arguments as for hallar_create;
+ * no options).  On success m (constraints), nnz_merged (stored entries of
+ * the merged CSR: off-diagonal C entries plus both orientations of every
+ * pair) and c_norm1 (induced 1-norm of C, the scale of eq. termination2)
+ * are written to the non-NULL host pointers.  Errors: HALLAR_EINVAL with
+ * the reason in hallar_last_error(NULL), HALLAR_ENOMEM. */
+hallar_status hallar_check_problem(int64_t n, int64_t n1, const int64_t* C_rowptr,
+                                   const int32_t* C_col, const double* C_val, double C_J,
+                                   double C_I, int32_t family, int64_t m_pairs,
+                                   const int32_t* cons_i, const int32_t* cons_j,
+                                   int32_t has_trace_row, const double* b, double tau2,
+                                   int64_t* m, int64_t* nnz_merged, double* c_norm1);
+
 /* Problem sizes of a handle (host pointers; any may be NULL). */
 hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz_merged,
                                int32_t* precision);

@@ -735,6 +735,30 @@ hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz,
   return HALLAR_OK;
 }
 
+hallar_status hallar_check_problem(int64_t n, int64_t n1, const int64_t* C_rowptr,
+                                   const int32_t* C_col, const double* C_val, double C_J,
+                                   double C_I, int32_t family, int64_t m_pairs,
+                                   const int32_t* cons_i, const int32_t* cons_j,
+                                   int32_t has_trace_row, const double* b, double tau2,
+                                   int64_t* m, int64_t* nnz_merged, double* c_norm1) {
+  g_create_error.clear();
+  try {
+    HostProblem hp;
+    merge_problem(hp, n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, m_pairs, cons_i,
+                  cons_j, has_trace_row, b, tau2);
+    if (m) *m = hp.m;
+    if (nnz_merged) *nnz_merged = hp.nnz;
+    if (c_norm1) *c_norm1 = hp.c_norm1;
+    return HALLAR_OK;
+  } catch (const Err& e) {
+    g_create_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    return HALLAR_ENOMEM;
+  }
+}
+
 void hallar_destroy(hallar_t h) { release(h); }
 
 const char* hallar_last_error(hallar_t h) {

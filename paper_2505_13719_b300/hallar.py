@@ -30,7 +30,7 @@ EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_
             "hallar_server_submit", "hallar_server_wait", "hallar_server_get_stats",
             "hallar_server_destroy", "hallar_server_last_error", "hallar_batch_create",
             "hallar_batch_layout", "hallar_batch_grad", "hallar_batch_shape",
-            "hallar_batch_destroy", "hallar_batch_last_error")
+            "hallar_batch_destroy", "hallar_batch_last_error", "hallar_check_problem")
 
 
 class hallar_options(C.Structure):
@@ -112,6 +112,8 @@ def _load():
         "hallar_server_get_stats": ([P, P], C.c_int),
         "hallar_server_destroy": ([P], None),
         "hallar_server_last_error": ([P], C.c_char_p),
+        "hallar_check_problem": ([I64, I64, P, P, P, D, D, I32, I64, P, P, I32, P, D, P, P, P],
+                                 C.c_int),
         "hallar_batch_create": ([I32, P, I32, I32, P, C.POINTER(C.c_void_p)], C.c_int),
         "hallar_batch_layout": ([P, P, P, P, P], C.c_int),
         "hallar_batch_grad": ([P, P, I32, P, P, P, P, P], C.c_int),
@@ -185,6 +187,32 @@ def hallar_create(n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, cons_i, cons_
                             C.byref(opt) if opt is not None else None, C.byref(h))
     _check(st, None)
     return h
+
+
+def hallar_check_problem(n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, cons_i, cons_j,
+                         has_trace_row, b, tau2):
+    """Host-only validation and merge (see hallar.h): (m, nnz_merged, c_norm1)."""
+    fam = FAMILY[family] if isinstance(family, str) else int(family)
+    rp = None if C_rowptr is None else np.ascontiguousarray(C_rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray([] if C_col is None else C_col, dtype=np.int32)
+    cv = np.ascontiguousarray([] if C_val is None else C_val, dtype=np.float64)
+    pi = np.ascontiguousarray(cons_i, dtype=np.int32)
+    pj = np.ascontiguousarray(cons_j, dtype=np.int32)
+    bb = np.ascontiguousarray(b, dtype=np.float64)
+    m_pairs = 0 if fam == HALLAR_DIAG else int(pi.shape[0])
+    m, nnz, cn = C.c_int64(), C.c_int64(), C.c_double()
+    st = _lib.hallar_check_problem(int(n), int(n1), _ptr(rp), _ptr(ci), _ptr(cv), float(C_J),
+                                   float(C_I), fam, m_pairs, _ptr(pi), _ptr(pj),
+                                   int(bool(has_trace_row)), _ptr(bb), float(tau2),
+                                   C.byref(m), C.byref(nnz), C.byref(cn))
+    _check(st, None)
+    return m.value, nnz.value, cn.value
+
+
+def check_instance(inst):
+    return hallar_check_problem(inst.n, inst.n1, inst.C_rowptr, inst.C_col, inst.C_val,
+                                inst.C_J, inst.C_I, inst.family, inst.cons_i, inst.cons_j,
+                                inst.has_trace_row, inst.b, inst.tau2)
 
 
 def hallar_eval_A(h, U, r, T):
