@@ -53,6 +53,13 @@
  *
  * Limits.  n < 2^31, stored nonzeros < 2^31, r <= 256; hallar_solve takes
  * r_cap <= 89 (its rank trim diagonalises an (r_cap+1)^2 Gram matrix).
+ *
+ * Beyond the single problem (none of these has a counterpart in the paper):
+ * hallar_server_* runs whole solves concurrently under an HBM budget
+ * (continuous batching), hallar_batch_* evaluates the fused operator of many
+ * stacked instances in one launch, hallar_check_problem validates a problem
+ * on the host alone, and hallar_grad_diag_noalloc is a handle-free gradient
+ * that allocates nothing.
  */
 #ifndef HALLAR_H
 #define HALLAR_H
