@@ -78,7 +78,9 @@ def constraint_entries(inst):
 
 
 def cost_entries(inst):
-    """Stored entries (a, b, value) of the sparse part of C (CSR expanded)."""
+    """Stored entries (a, b, value) of the sparse part of C (CSR expanded);
+    C is the cost matrix of (P) (Section 1, eq. P), C_J 11^T and C_I I are
+    implicit and handled by the callers."""
     rowptr = inst.C_rowptr.astype(np.int64)
     a = np.repeat(np.arange(inst.n, dtype=np.int64), np.diff(rowptr))
     return a, inst.C_col.astype(np.int64), inst.C_val.astype(np.float64)
@@ -174,7 +176,9 @@ def al_grad(inst, U, p, beta):
 
 def _magnitude(inst, U, ps, T):
     """sum_l |p'_l| |A_l.UU^T| plus the absolute values of the terms of
-    C.UU^T: the size of the terms whose rounding perturbs g."""
+    C.UU^T: the size of the terms whose rounding perturbs g.  Not in the
+    paper: it scales the rounding allowance of the ADAP-FISTA and ADAP-AIPP
+    step-2 tests (a floating-point reading)."""
     a, b, v = cost_entries(inst)
     mag = float(np.abs(ps) @ np.abs(T[1:]))
     if v.shape[0]:
@@ -207,6 +211,8 @@ def _pair_change(X, Y, D, a, b):
 
 
 def _pair_dots_mixed(P, Q, a, b, chunk=1 << 20):
+    """<P_a,:, Q_b,:> for each listed pair (the pair products of Section 4.1
+    with two different factors)."""
     out = np.empty(a.shape[0])
     for s in range(0, a.shape[0], chunk):
         e = min(s + chunk, a.shape[0])
