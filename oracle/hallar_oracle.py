@@ -26,9 +26,11 @@ Pins (tests/test_oracle_*.py): operators against dense brute force, the
 adjoint identity, finite differences and the Max-Cut cut identity; Lanczos
 against dense eigendecomposition and the closed-form torus and hypercube
 spectra; the Frank-Wolfe step as an exact line search; ADAP-AIPP's output
-invariants; full solves against closed-form SDP values with a dense dual
-certificate; ``splitmix64_uniform`` against the generator's published output
-words from state 0.  Parity unpinned: iteration counts and trajectories (they
+invariants; ADAP-FISTA against the closed-form prox point of a quadratic;
+the KKT measures at a closed-form optimal primal-dual pair; full solves
+against closed-form SDP values with a dense dual certificate;
+``splitmix64_uniform`` against the generator's published output words from
+state 0.  Parity unpinned: iteration counts and trajectories (they
 follow the readings, not the paper).
 """
 from __future__ import annotations
