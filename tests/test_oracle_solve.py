@@ -221,3 +221,20 @@ def test_adap_fista_on_a_quadratic_with_a_closed_form_prox():
     def psi(U):
         return lam * c * float(np.sum(U * U)) + 0.5 * float(np.sum((U - U0) ** 2))
     assert psi(y) < psi(U0)
+
+
+def test_rank_trim_is_the_best_low_rank_approximation():
+    # Eckart-Young: Y Q_k (Q_k the top-k eigenvectors of Y^T Y) gives
+    # X_k = Y Q_k Q_k^T Y^T, the best rank-k approximation of X = Y Y^T, whose
+    # Frobenius error is sqrt(sum_{i>k} s_i^4) with s the singular values of
+    # Y (eigenvalues of X are s_i^2); the remainder X - X_k is psd
+    rng = np.random.default_rng(3)
+    Y = rng.standard_normal((40, 7)) @ np.diag([3.0, 2.5, 2.0, 1.5, 1.0, 0.5, 0.25])
+    s = np.linalg.svd(Y, compute_uv=False)
+    X = Y @ Y.T
+    for k in (1, 3, 6):
+        Yk = O.trim_rank(Y, k)
+        assert Yk.shape == (40, k)
+        Xk = Yk @ Yk.T
+        assert np.linalg.norm(X - Xk) == pytest.approx(math.sqrt(np.sum(s[k:] ** 4)), rel=1e-10)
+        assert np.linalg.eigvalsh(X - Xk)[0] >= -1e-10 * s[0] ** 2
