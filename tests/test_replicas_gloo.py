@@ -69,3 +69,12 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    # the reference line's contract: the same metric and unit as the main
+    # arm, a cpu_baseline describing this run, an e2e with no copies
+    for key in ("metric", "unit", "steps", "warmup", "higher_is_better", "config", "dtype"):
+        assert key in d, key
+    assert d["higher_is_better"] is False and d["unit"] == "s"
+    cb = d["cpu_baseline"]
+    assert cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
