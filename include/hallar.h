@@ -167,6 +167,36 @@ hallar_status hallar_eval_A(hallar_t h, const void* U, int32_t r, double* T);
 hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
                           double beta, void* W, double* g_val, double* resid);
 
+/* Change of the AL value g(U) = L_beta(UU^T; p) between two factors,
+ * g(Y) - g(X) (eq. AL function): the quantity the step-2 tests of ADAP-FISTA
+ * (Appendix A.1) and ADAP-AIPP (Appendix A) compare.  It is formed without
+ * cancellation from the differences of the pair products,
+ * <Y_a,Y_b> - <X_a,X_b> = <D_a,Y_b> + <X_a,D_b> with D = Y - X, by the same
+ * kernel hallar_solve runs.
+ *   X, Y  [n x r] factors (host or device, the handle's precision), r in [1, 256].
+ *   p     [m] multipliers (doubles), beta the penalty.
+ *   rX    [m] r_X = A(XX^T) - b (doubles, host or device), or NULL: then the
+ *         library evaluates it with one pass of the fused operator.
+ *   dg    (host) receives g(Y) - g(X).
+ *   rY    [m] out (doubles, host or device) or NULL: r_Y = r_X + A(YY^T) - A(XX^T).
+ * In the mixed form p and r_X are read as float copies and r_Y is formed in
+ * float (the solver keeps its residuals in the factor type). */
+hallar_status hallar_value_change(hallar_t h, const void* X, const void* Y, int32_t r,
+                                  const double* p, double beta, const double* rX, double* dg,
+                                  double* rY);
+
+/* Rank trim (not in the paper; the solver applies it when a Frank-Wolfe step
+ * (eq. tilde Y) would take the factor above hallar_options.r_cap):
+ * Yout = Y Q_k, where Q_k holds the k leading eigenvectors of the Gram Y^T Y,
+ * so Yout Yout^T is the best rank-k approximation of YY^T (Eckart-Young).
+ *   Y     [n x r] (host or device, the handle's precision), 1 <= k <= r <= 90.
+ *   Yout  [n x k] out (host or device), leading dimension k.
+ *   eigs  [r] out (host, may be NULL): the Gram eigenvalues, descending.
+ * The Gram is accumulated in FP64; its eigenvectors come from cyclic Jacobi
+ * rotations on the host. */
+hallar_status hallar_trim_rank(hallar_t h, const void* Y, int32_t r, int32_t k, void* Yout,
+                               double* eigs);
+
 /* Minimum eigenpair of G = C + A*(p') (Alg. 1 step 7, eq. Grad X Space) by
  * Lanczos in FP64 with partial reorthogonalisation (the basis is swept
  * against when Simon's estimate of the loss of orthogonality passes
@@ -202,19 +232,31 @@ hallar_status hallar_get_solution(hallar_t h, void* U, int32_t r_capacity, doubl
  * value-change kernel of the ADAP-FISTA / ADAP-AIPP tests, 2 = the Lanczos
  * basis passes.  op = 1 clears the counters and starts timing (a CUDA event
  * pair on the handle's stream around every launch of those kernels), op = 2
- * stops timing, op = 0 only reads.  ms[3], launches[3] and bytes[3] (host,
- * may be NULL) receive, per class since the last clear, the summed kernel
- * milliseconds, the launch counts and the summed algorithmic bytes (every
- * input array read once and every output written once; gathered neighbour
- * rows are not counted).  Timing adds two event records per launch. */
+ * stops timing, op = 0 only reads.  ms[3], launches[3], bytes[3] and
+ * bytes_padded[3] (host, may be NULL) receive, per class since the last
+ * clear, the summed kernel milliseconds, the launch counts and the summed
+ * bytes: every input array read once and every output written once,
+ * gathered neighbour rows not counted; `bytes` counts the r columns of each
+ * factor row and per-row / per-constraint vectors at the element size the
+ * kernel reads (4 bytes in the mixed form), `bytes_padded` the stored
+ * leading dimension (r rounded up to 16 bytes) instead of r.  Timing adds
+ * two event records per timed launch (see hallar_profile_sampling). */
 hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launches,
-                             double* bytes);
+                             double* bytes, double* bytes_padded);
+
+/* Sampled kernel timing: with every = k > 1, hallar_profile times only every
+ * k-th launch of each kernel class (the 1st, (k+1)-th, ...) and counts the
+ * bytes and launches of the timed ones, so the average launch duration is
+ * measured at 1/k of the event overhead.  every = 1 (the default) times
+ * every launch.  HALLAR_EINVAL for every < 1. */
+hallar_status hallar_profile_sampling(hallar_t h, int32_t every);
 
 /* Allocation-free fused gradient for the diagonal (Max-Cut) family.  The
  * paper has no counterpart: it exists for callers that cannot let a library
- * call cudaMalloc -- code running while a stream is captured into a CUDA
- * graph, code that hands out device memory only from its own pool, hot
- * paths that must not touch the allocator.  It computes what hallar_grad
+ * call cudaMalloc -- applications that hand out device memory only from their
+ * own pool or arena and account for every byte, and hot paths where an
+ * allocation (or the device-wide synchronisation of a later cudaFree) would
+ * stall work queued on other streams.  It computes what hallar_grad
  * computes for a HALLAR_DIAG problem (A_i = e_i e_i^T, b, C), from arrays
  * the caller owns, with no handle:
  *   rowptr[n+1], col[nnz], cval[nnz]  off-diagonal entries of C (device,
@@ -234,8 +276,9 @@ hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launch
  * it keeps the last call's contents, the counter is cleared at the start of
  * each call, and calls whose kernels overlap on the GPU race on it.  The
  * first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. */
+ * (cudaGetSymbolAddress) with that device current, and looks it up again
+ * when the device's context was re-created (after cudaDeviceReset); make
+ * that first call before any stream capture. */
 hallar_status hallar_grad_diag_noalloc(int64_t n, int32_t r, const int32_t* rowptr,
                                        const int32_t* col, const double* cval,
                                        const double* cdiag, const double* b, const double* p,

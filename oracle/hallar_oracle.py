@@ -397,10 +397,15 @@ class Counters:
 
 
 class _Subproblem:
-    """g_t(U) = L_beta(UU^T; p) on the ball B_tau^s (eq. Lr / g func)."""
+    """g_t(U) = L_beta(UU^T; p) on the ball B_tau^s (eq. Lr / g func).
 
-    def __init__(self, inst, p, beta, cnt):
+    ``observer`` (None by default) is called as observer(event, data) when a
+    step-2 test of ADAP-FISTA or ADAP-AIPP accepts; it only reads, so the
+    tests can recheck each accepted inequality in exact arithmetic."""
+
+    def __init__(self, inst, p, beta, cnt, observer=None):
         self.inst, self.p, self.beta, self.cnt = inst, p, beta, cnt
+        self.observer = observer
 
     def grad(self, U):
         self.cnt.grads += 1
@@ -453,6 +458,10 @@ def adap_fista(sub, lam, center, mu, L0, opt, tau):
             slack = ROUND_SLACK * UNIT_ROUNDOFF * lam * gr.mag
             if float(np.sum(dpsi_xt * d)) + (1.0 - opt.chi) * Ln / 4.0 * float(np.sum(d * d)) \
                     >= dpsi - slack:
+                if sub.observer is not None:
+                    sub.observer("fista_step2", dict(xt=xt, y=ynew, center=center, lam=lam,
+                                                     L=Ln, chi=opt.chi, slack=slack,
+                                                     mag=gr.mag))
                 break
             Ln *= 2.0
             if Ln > 1e30:
@@ -514,6 +523,9 @@ def adap_aipp(sub, W0, rho, state, opt, tau):
                 lhs = -state.lam * dg - 0.5 * d2
                 slack = ROUND_SLACK * UNIT_ROUNDOFF * state.lam * mag
                 if stalled or lhs >= -float(np.sum(V * D)) - slack:     # step 2
+                    if sub.observer is not None:
+                        sub.observer("aipp_step2", dict(Wprev=Wprev, W=W, V=V, lam=state.lam,
+                                                        stalled=stalled, slack=slack, mag=mag))
                     break
             state.lam /= 2.0
             if state.lam < 1e-30:

@@ -88,9 +88,11 @@ void fetch_scalars(Ctx* c, int first, int count) {
   sync(c);
 }
 
-int prof_begin(Ctx* c, int cls, double bytes) {
+int prof_begin(Ctx* c, int cls, OpBytes bytes) {
   if (!c->prof_on) return -1;
-  c->prof_bytes[cls] += bytes;
+  if (c->prof_seen[cls]++ % c->prof_every != 0) return -1;  // not sampled
+  c->prof_bytes[cls] += bytes.alg;
+  c->prof_bytes_pad[cls] += bytes.pad;
   // the pool is reused: pending pair q uses events 2q and 2q + 1
   const size_t idx = c->prof_pending.size();  // two entries per pending pair
   while (c->prof_pool.size() < idx + 2) {
@@ -633,6 +635,120 @@ hallar_status hallar_grad(hallar_t h, const void* U, int32_t r, const double* p,
   });
 }
 
+hallar_status hallar_value_change(hallar_t h, const void* X, const void* Y, int32_t r,
+                                  const double* p, double beta, const double* rX, double* dg,
+                                  double* rY) {
+  return guarded(h, [&]() -> hallar_status {
+    Ctx* c = h;
+    if (!X || !Y || !p || !dg || r < 1 || r > 256 || !std::isfinite(beta))
+      fail(HALLAR_EINVAL, "hallar_value_change: bad argument");
+    const bool mixed = c->opt.precision == HALLAR_MIXED;
+    const int ld = padded_ld(c, r);
+    const int64_t n = c->P.n, m = c->P.m;
+    const size_t es = elem_size(c);
+    // X through the regular staging buffer, Y through a second one
+    const void* Xd = stage_factor(c, X, r, ld);
+    const void* Yd = Y;
+    if (!(is_device_ptr(Y) && r == ld && ((uintptr_t)Y % 16) == 0)) {
+      const void* src = Y;
+      if (!is_device_ptr(Y)) {
+        void* raw = ensure_buffer(c, &c->stage_wout, &c->stage_wout_bytes, (size_t)n * r * es);
+        HL_CUDA(cudaMemcpyAsync(raw, Y, (size_t)n * r * es, cudaMemcpyHostToDevice, c->stream));
+        src = raw;
+      }
+      if (r == ld) {
+        Yd = src;
+      } else {
+        void* dst = ensure_buffer(c, &c->stage_y, &c->stage_y_bytes, (size_t)n * ld * es);
+        launch_pad_copy(c, src, r, dst, ld, r, 1.0);
+        Yd = dst;
+      }
+    }
+    const double* pd = stage_dvec(c, p, m, &c->stage_m1, &c->stage_m1_bytes);
+    // r_X: given, or from one pass of the fused operator at X
+    double* rxd = (double*)ensure_buffer(c, (void**)&c->stage_m0, &c->stage_m0_bytes,
+                                         (size_t)m * sizeof(double));
+    // factor-typed copies of p, r_X and the output r_Y (p, r_X and r_Y
+    // themselves in FP64)
+    void* pk = (void*)pd;
+    void* rxk = rxd;
+    void* ryk = nullptr;
+    if (mixed) {
+      void* buf = ensure_buffer(c, &c->stage_pk, &c->stage_pk_bytes, 3 * (size_t)m * sizeof(float));
+      pk = buf;
+      rxk = (float*)buf + m;
+      ryk = (float*)buf + 2 * m;
+      launch_to_factor_type(c, m, pk, pd);
+    }
+    double* ryd = nullptr;
+    if (rY) {
+      ryd = is_device_ptr(rY) ? rY
+                              : (double*)ensure_buffer(c, (void**)&c->stage_vc, &c->stage_vc_bytes,
+                                                       (size_t)m * sizeof(double));
+      if (!mixed) ryk = ryd;
+    }
+    if (rX) {
+      HL_CUDA(cudaMemcpyAsync(rxd, rX, m * sizeof(double),
+                              is_device_ptr(rX) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+      if (mixed) launch_to_factor_type(c, m, rxk, rxd);
+    } else {
+      if (c->P.C_J != 0.0 || c->P.has_trace) launch_colsum(c, Xd, ld, c->d_colsum, S_PRE);
+      launch_grad(c, Xd, ld, r, pk, 0.0, GradOut{nullptr, rxk, nullptr});
+      if (c->P.has_trace) {
+        HL_CUDA(cudaMemcpyAsync(c->h_scal + S_SCALE + 4, c->P.b + (m - 1), sizeof(double),
+                                cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        launch_trace_fix(c, rxk, nullptr, c->d_scal + S_PRE, -c->h_scal[S_SCALE + 4]);
+      }
+      if (mixed) launch_to_double(c, m, rxd, rxk);
+    }
+    // the pieces of g(Y) - g(X), as the solver forms them
+    if (c->P.C_J != 0.0)
+      launch_colsum_diff(c, Xd, Yd, ld, c->d_colsum + kColsumMax, c->d_colsum + 2 * kColsumMax);
+    launch_value_change(c, Xd, Yd, ld, r, pk, rxk, ryk);
+    if (ryk && c->P.has_trace) launch_trace_fix(c, ryk, rxk, c->d_scal + S_DIFF + 3, 0.0);
+    if (mixed && ryk) launch_to_double(c, m, ryd, ryk);
+    fetch_scalars(c, 0, S_COUNT);
+    const double* hs = c->h_scal;
+    const double dT0 = hs[S_DIFF] + (c->P.C_J != 0.0 ? c->P.C_J * hs[S_DIFF + 5] : 0.0);
+    double pdT = hs[S_DIFF + 1], q = hs[S_DIFF + 2];
+    if (c->P.has_trace) {
+      double pt = 0.0, rxt = 0.0;
+      HL_CUDA(cudaMemcpyAsync(&pt, pd + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+      HL_CUDA(cudaMemcpyAsync(&rxt, rxd + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+      HL_CUDA(cudaStreamSynchronize(c->stream));
+      const double dt = hs[S_DIFF + 3];
+      pdT += pt * dt;
+      q += dt * (2.0 * rxt + dt);
+    }
+    *dg = dT0 + pdT + 0.5 * beta * q;
+    if (rY && ryd != rY) copy_out_dvec(c, rY, ryd, m);
+    sync(c);
+    return HALLAR_OK;
+  });
+}
+
+hallar_status hallar_trim_rank(hallar_t h, const void* Y, int32_t r, int32_t k, void* Yout,
+                               double* eigs) {
+  return guarded(h, [&]() -> hallar_status {
+    Ctx* c = h;
+    if (!Y || !Yout || r < 1 || r > 90 || k < 1 || k > r)
+      fail(HALLAR_EINVAL, "hallar_trim_rank: need 1 <= k <= r <= 90 and non-NULL Y, Yout");
+    const int ld = padded_ld(c, r);
+    const int ldk = padded_ld(c, k);
+    const int64_t n = c->P.n;
+    const void* Yd = stage_factor(c, Y, r, ld);
+    void* out = ensure_buffer(c, &c->stage_y, &c->stage_y_bytes, (size_t)n * ldk * elem_size(c));
+    trim_factor(c, Yd, ld, r, k, out, ldk, eigs);
+    unstage_factor(c, out, ldk, Yout, k);
+    sync(c);
+    return HALLAR_OK;
+  });
+}
+
 hallar_status hallar_min_eig(hallar_t h, const double* pshift, double tol, int32_t kmax,
                              const double* v0, double* lambda_min, double* v, int32_t* iters,
                              double* resid) {
@@ -700,7 +816,7 @@ hallar_status hallar_get_solution(hallar_t h, void* U, int32_t r_capacity, doubl
 }
 
 hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launches,
-                             double* bytes) {
+                             double* bytes, double* bytes_padded) {
   return guarded(h, [&]() -> hallar_status {
     Ctx* c = h;
     if (op < 0 || op > 2) fail(HALLAR_EINVAL, "hallar_profile: op must be 0, 1 or 2");
@@ -711,16 +827,28 @@ hallar_status hallar_profile(hallar_t h, int32_t op, double* ms, int64_t* launch
       for (int k = 0; k < 3; ++k) launches[k] = c->prof_n[k];
     if (bytes)
       for (int k = 0; k < 3; ++k) bytes[k] = c->prof_bytes[k];
+    if (bytes_padded)
+      for (int k = 0; k < 3; ++k) bytes_padded[k] = c->prof_bytes_pad[k];
     if (op == 1) {
       for (int k = 0; k < 3; ++k) {
         c->prof_ms[k] = 0.0;
         c->prof_n[k] = 0;
         c->prof_bytes[k] = 0.0;
+        c->prof_bytes_pad[k] = 0.0;
+        c->prof_seen[k] = 0;
       }
       c->prof_on = true;
     } else if (op == 2) {
       c->prof_on = false;
     }
+    return HALLAR_OK;
+  });
+}
+
+hallar_status hallar_profile_sampling(hallar_t h, int32_t every) {
+  return guarded(h, [&]() -> hallar_status {
+    if (every < 1) fail(HALLAR_EINVAL, "hallar_profile_sampling: every must be >= 1");
+    h->prof_every = every;
     return HALLAR_OK;
   });
 }

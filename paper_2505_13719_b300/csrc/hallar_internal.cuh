@@ -75,6 +75,12 @@ struct RedBuf {
   unsigned* counter = nullptr;
 };
 
+// bytes of one timed kernel launch (see op_bytes in kernels_ops.cu): alg with
+// the factor's r columns, pad with its stored leading dimension
+struct OpBytes {
+  double alg = 0.0, pad = 0.0;
+};
+
 // device scalar slots (doubles), mirrored to pinned host memory
 enum Slot : int {
   S_GRAD = 0,    // fused operator: C.UU^T part, p.r, r.r
@@ -114,8 +120,11 @@ struct hallar_ctx {
   double* stage_p0 = nullptr; size_t stage_p0_bytes = 0;
   void* stage_pk = nullptr; size_t stage_pk_bytes = 0;
   void* stage_T = nullptr; size_t stage_T_bytes = 0;     // constraint values in the factor type
+  void* stage_y = nullptr; size_t stage_y_bytes = 0;     // second factor (value change, trim)
+  double* stage_vc = nullptr; size_t stage_vc_bytes = 0; // r_Y of hallar_value_change
   void* eig_stage = nullptr; size_t eig_stage_bytes = 0;
   void* gram_part = nullptr; size_t gram_part_bytes = 0;
+  void* trim_gram = nullptr; size_t trim_gram_bytes = 0;
   // Lanczos workspace (basis, vectors, partial rows)
   void* lan_Q = nullptr; size_t lan_Q_bytes = 0;
   void* lan_w = nullptr; size_t lan_w_bytes = 0;
@@ -123,8 +132,11 @@ struct hallar_ctx {
   void* lan_h = nullptr; size_t lan_h_bytes = 0;
   // kernel timing (hallar_profile): event pairs pending per kernel class
   bool prof_on = false;
+  int prof_every = 1;                 // time every prof_every-th launch of a class
+  int64_t prof_seen[3] = {0, 0, 0};   // launches of each class since the last clear
   double prof_ms[3] = {0.0, 0.0, 0.0};
   double prof_bytes[3] = {0.0, 0.0, 0.0};  // algorithmic bytes of the timed launches
+  double prof_bytes_pad[3] = {0.0, 0.0, 0.0};  // the same with padded factor rows
   int64_t prof_n[3] = {0, 0, 0};
   std::vector<cudaEvent_t> prof_pool;
   std::vector<int> prof_pending;  // (class, start event index), stop = start + 1
@@ -186,7 +198,7 @@ void* ensure_buffer(Ctx* c, void** buf, size_t* cur_bytes, size_t bytes);
 void sync(Ctx* c);
 // kernel timing: prof_begin records a start event and returns its token (or
 // -1 when timing is off); prof_end records the stop event of that token
-int prof_begin(Ctx* c, int cls, double bytes);
+int prof_begin(Ctx* c, int cls, OpBytes bytes);
 void prof_end(Ctx* c, int token);
 void prof_resolve(Ctx* c);  // after a stream sync: add finished pairs
 void fetch_scalars(Ctx* c, int first, int count);  // d_scal -> h_scal, then sync
@@ -211,8 +223,8 @@ struct GradOut {
   double* T = nullptr;      // [m+1] or null (T[0] and the trace row by the caller)
 };
 
-// algorithmic bytes of one launch of the fused operator (see kernels_ops.cu)
-double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool reads_p);
+OpBytes op_bytes(const Ctx* c, int r, int ld, int factor_arrays, bool writes_resid, bool reads_p,
+                 bool reads_rx);
 // pre-pass: colsum of U into colsum_out, S_PRE[0] = |U|_F^2, S_PRE[1] = |colsum|^2,
 // and C_J * colsum in the factor type at cj_row (kColsumMax entries) when C_J != 0
 void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot);
@@ -282,8 +294,16 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
                            int max_restarts, double* v_out);
 void launch_splitmix(Ctx* c, uint64_t seed, double* out, double mix_scale, const double* base);
 
+// trace-row entry of a residual vector (factor type) from a device scalar:
+// r[m-1] = (src ? src[m-1] : 0) + *dscal + add
+void launch_trace_fix(Ctx* c, void* r, const void* src, const double* dscal, double add);
+
 // solver (solver.cu)
 hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_result* res);
+// rank trim: out (n x ld_out) = Y Q_k, Q_k the k leading eigenvectors of
+// Y^T Y; eigs (host, may be null) gets the r Gram eigenvalues, descending
+void trim_factor(Ctx* c, const void* Y, int ld, int r, int k, void* out, int ld_out,
+                 double* eigs);
 
 // ---------------------------------------------------------------------------
 // grid sizing: a fixed grid per (work, items per block) so that reductions

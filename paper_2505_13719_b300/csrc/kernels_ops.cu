@@ -578,23 +578,31 @@ Shape pick_shape(int ld, int vec) {
 
 }  // namespace
 
-// algorithmic bytes of one operator launch: the factor row (and W) once, the
-// merged CSR once, the per-row and per-constraint vectors once
-double op_bytes(const Ctx* c, int ld, bool writes_w, bool writes_resid, bool reads_p) {
+// Bytes of one operator launch: the factor rows (and W) once, the merged CSR
+// once, the per-row and per-constraint vectors once; gathered neighbour rows
+// are not counted.  alg counts the r columns of the factor and the element
+// size the kernel reads per-row vectors in (4 bytes in the mixed form, 8 in
+// FP64); pad counts the stored leading dimension ld instead of r.
+OpBytes op_bytes(const Ctx* c, int r, int ld, int factor_arrays, bool writes_resid,
+                 bool reads_p, bool reads_rx) {
   const Problem& P = c->P;
   const double es = (double)elem_size(c);
-  double b = (double)P.n * ld * es * (writes_w ? 2.0 : 1.0);
+  double b = 0.0;
   b += (double)P.nnz * 4.0;                                      // column indices
   if (P.code) b += (double)P.nnz * 4.0;                          // constraint codes
   if (P.fam != FAM_EDGE) b += (double)P.nnz * es;                // C values
-  b += (double)(P.n + 1) * 4.0 + (double)P.n * 8.0;              // row pointers, diagonal
-  b += (double)P.m * 8.0 * (1.0 + (reads_p ? 1.0 : 0.0) + (writes_resid ? 1.0 : 0.0));  // b, p, r
-  return b;
+  b += (double)(P.n + 1) * 4.0 + (double)P.n * es;               // row pointers, diagonal
+  const double mv = 1.0 + (reads_p ? 1.0 : 0.0) + (writes_resid ? 1.0 : 0.0) +
+                    (reads_rx ? 1.0 : 0.0);
+  b += (double)P.m * es * mv;                                    // b, p, r_X, r
+  OpBytes o;
+  o.alg = b + (double)P.n * r * es * factor_arrays;
+  o.pad = b + (double)P.n * ld * es * factor_arrays;
+  return o;
 }
 
 void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
                  GradOut out) {
-  (void)r;
   if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
   OpArgs a = make_args(c, ld, S_GRAD);
   a.p = p;
@@ -613,7 +621,8 @@ void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double bet
     tout = mixed ? ensure_buffer(c, &c->stage_T, &c->stage_T_bytes, (size_t)c->P.m * sizeof(float))
                  : (void*)(out.T + 1);
   io.Tout = tout;
-  const int tok = prof_begin(c, 0, op_bytes(c, ld, out.W != nullptr, out.resid != nullptr, true));
+  const int tok = prof_begin(c, 0, op_bytes(c, r, ld, out.W != nullptr ? 2 : 1,
+                                            out.resid != nullptr, true, false));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
     if (io.cjv != nullptr) {
       const int grid = wave_grid(c, k_grad<T, FAM, G, K, true>, a.n, kBlock / G, kBlock);
@@ -630,12 +639,10 @@ void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double bet
 
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const void* p,
                          const void* rX, void* rY) {
-  (void)r;
   OpArgs a = make_args(c, ld, S_DIFF);
   a.p = p;
   DiffIO io{X, Y, rX, rY};
-  const int tok = prof_begin(c, 1, op_bytes(c, ld, false, rY != nullptr, true) +
-                                       (double)c->P.n * ld * (double)elem_size(c));
+  const int tok = prof_begin(c, 1, op_bytes(c, r, ld, 2, rY != nullptr, true, true));
   HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
     const int grid = wave_grid(c, k_value_change<T, FAM, G, K>, a.n, kBlock / G, kBlock);
     k_value_change<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);

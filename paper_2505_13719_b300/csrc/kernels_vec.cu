@@ -341,6 +341,13 @@ __global__ void k_right_mult(const T* __restrict__ U, int ld, int r, const doubl
   }
 }
 
+// r[0] = (src ? src[0] : 0) + *dscal + add (trace-row residual entry)
+template <class T>
+__global__ void k_trace_fix(T* dst, const T* src, const double* dscal, double add) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    dst[0] = (T)((src ? (double)src[0] : 0.0) + dscal[0] + add);
+}
+
 // run the statements with T the factor element type of the handle
 #define HL_BY_TYPE(c, ...)                                    \
   do {                                                        \
@@ -411,6 +418,13 @@ void launch_norm2(Ctx* c, const void* U, int ld, int slot) {
 void launch_dot(Ctx* c, const void* W, const void* U, int ld, int slot) {
   const int64_t ne = c->P.n * (int64_t)ld;
   HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpDot<T>{{}, (const T*)W, (const T*)U}, slot));
+}
+
+void launch_trace_fix(Ctx* c, void* r, const void* src, const double* dscal, double add) {
+  const int64_t m = c->P.m;
+  HL_BY_TYPE(c, k_trace_fix<T><<<1, 32, 0, c->stream>>>(
+                    (T*)r + (m - 1), src ? (const T*)src + (m - 1) : nullptr, dscal, add));
+  HL_CHECK_LAUNCH(c);
 }
 
 void launch_axpy_t(Ctx* c, int64_t len, double* a, const double* b, const void* t, double s) {

@@ -33,6 +33,13 @@ namespace {
 
 constexpr int kLanMaxCols = 512;  // 16 accumulators per lane
 
+// Lanczos vectors are unpadded FP64 n-vectors: algorithmic = stored bytes
+OpBytes lan_bytes(double b) {
+  OpBytes o;
+  o.alg = o.pad = b;
+  return o;
+}
+
 struct LanArgs {
   int64_t n;
   const int* __restrict__ rowptr;
@@ -461,7 +468,7 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
     for (int k = 0; k < kmax; ++k) {
       const int ncols = k + 1;
       // step 1 and step 2 (three-term recurrence)
-      const int tok1 = prof_begin(c, 2, 40.0 * n + 12.0 * (double)c->P.nnz + 8.0 * c->P.m);
+      const int tok1 = prof_begin(c, 2, lan_bytes(40.0 * n + 12.0 * (double)c->P.nnz + 8.0 * c->P.m));
       k_lan_step1<<<grid_row, kBlock, 0, c->stream>>>(a, vin, vscale, vsum, prev, pscale, bprev, Q,
                                                      kcap, k, c->red.partials, c->red.counter,
                                                      d_alpha);
@@ -498,7 +505,7 @@ LanczosOut lanczos_min_eig(Ctx* c, const double* pshift, const double* v0, doubl
       }
       if (sweep && bnorm > 0.0) {
         // two classical Gram-Schmidt sweeps of w against q_0 .. q_k
-        const int tok2 = prof_begin(c, 2, 3.0 * (8.0 * n * ncols + 16.0 * n));
+        const int tok2 = prof_begin(c, 2, lan_bytes(3.0 * (8.0 * n * ncols + 16.0 * n)));
         HL_CUDA(cudaMemsetAsync(h2, 0, ncols * sizeof(double), c->stream));
         HL_BY_NACC(ncols, k_lan_orth<NACC><<<grid, kBlock, 0, c->stream>>>(n, Q, kcap, ncols, h2,
                                                                             prev, part));

@@ -1,11 +1,11 @@
 // Allocation-free fused gradient for the diagonal (Max-Cut) constraint family.
 //
 // The regular entry points run through a handle that owns device buffers it
-// allocates with cudaMalloc.  Some callers cannot allow that: code running
-// while a stream is being captured into a CUDA graph (cudaMalloc is not
-// permitted there), code that hands out device memory only from its own pool
-// or arena, and callers on a hot path that must not hit the allocator at
-// all.  hallar_grad_diag_noalloc serves them: the caller passes every input
+// allocates with cudaMalloc.  Some callers cannot allow that: applications
+// that hand out device memory only from their own pool or arena and account
+// for every byte, and hot paths where an allocation (or the device-wide
+// synchronisation of a later cudaFree) would stall work queued on other
+// streams.  hallar_grad_diag_noalloc serves them: the caller passes every input
 // and output array, and the only scratch the kernel needs -- the per-block
 // partial sums and the arrival counter of its grid reduction -- lives in the
 // file-scope device array below.
@@ -14,7 +14,8 @@
 // bytes (about 29 KB) until the process exits.  In host code its name is a
 // host-side stand-in, not a device address, so the host looks the device
 // address up with cudaGetSymbolAddress once per device (on the first call
-// on that device, with that device current) and passes it to the kernel.
+// on that device, with that device current; again after the device's
+// context was re-created) and passes it to the kernel.
 // All calls share the array and it keeps the last call's contents: each call
 // clears the arrival counter before its kernel, and calls whose kernels
 // overlap on the GPU race on the array.
@@ -39,9 +40,44 @@ static __device__ __align__(256) double g_noalloc_scratch[kNaScratchDoubles];
 struct DevState {
   double* scratch = nullptr;  // device address of g_noalloc_scratch
   int sms = 0;
+  unsigned long long ctx_id = 0;  // context the address belongs to (0: unknown)
 };
 std::mutex g_na_mu;
 DevState g_na_dev[kNaMaxDevices];
+
+// Unique ID of the calling thread's current CUDA context, or 0 when it cannot
+// be read.  A device reset or a destroyed and re-created primary context
+// reloads this module at a new address; comparing context IDs tells the
+// cached address is stale.  The driver calls are reached through the
+// runtime's entry-point query, so the library needs no link to libcuda.
+using CtxGetCurrentFn = int (*)(void**);
+using CtxGetIdFn = int (*)(void*, unsigned long long*);
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // under g_na_mu
+    looked_up = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || ctx == nullptr) return 0;
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 // Same arithmetic as the fused operator for the diagonal family: per row i,
 // |U_i|^2, r_i = |U_i|^2 - b_i, p'_i = p_i + beta r_i, W_i = sum_j C_ij U_j +
@@ -153,8 +189,12 @@ extern "C" hallar_status hallar_grad_diag_noalloc(
   {
     std::lock_guard<std::mutex> lock(g_na_mu);
     DevState& d = g_na_dev[dev];
+    const unsigned long long ctx_now = current_ctx_id();
+    if (d.scratch != nullptr && d.ctx_id != 0 && ctx_now != 0 && ctx_now != d.ctx_id)
+      d.scratch = nullptr;  // the context was re-created: look the address up again
     if (d.scratch == nullptr) {
-      // once per device, with that device current: the scratch's device address
+      // once per device (and context), with that device current: the
+      // scratch's device address
       void* ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess || ptr == nullptr) {
@@ -170,6 +210,7 @@ extern "C" hallar_status hallar_grad_diag_noalloc(
       }
       d.scratch = static_cast<double*>(ptr);
       d.sms = sms;
+      d.ctx_id = current_ctx_id();
     }
     st = d;
   }

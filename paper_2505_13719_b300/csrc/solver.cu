@@ -34,13 +34,6 @@ namespace hallar {
 
 namespace {
 
-// trace-row residual (factor type) from a device scalar: dst = src + dscal + add
-template <class T>
-__global__ void k_trace_fix(T* dst, const T* src, const double* dscal, double add) {
-  if (threadIdx.x == 0 && blockIdx.x == 0)
-    dst[0] = (T)((src ? (double)src[0] : 0.0) + dscal[0] + add);
-}
-
 // symmetric r x r eigendecomposition by cyclic Jacobi rotations (rank trim)
 void jacobi_eig(std::vector<double>& A, int r, std::vector<double>& V, std::vector<double>& w) {
   V.assign((size_t)r * r, 0.0);
@@ -101,7 +94,7 @@ struct Solver {
   // residual vectors have the factor type
   double *p = nullptr, *pshift = nullptr;
   void *pk = nullptr, *r_ctr = nullptr, *rX = nullptr, *rY = nullptr;
-  double *v = nullptr, *vprev = nullptr, *v0 = nullptr, *gram = nullptr;
+  double *v = nullptr, *vprev = nullptr, *v0 = nullptr;
   int rank = 0, ld = 0;
   double beta = 1.0, lam = 1.0, Mbar = 1.0, p_tr = 0.0, b_tr = 0.0;
   hallar_result R{};
@@ -141,7 +134,6 @@ struct Solver {
     v = salloc<double>(n);
     vprev = salloc<double>(n);
     v0 = salloc<double>(n);
-    gram = salloc<double>((size_t)ld_max * ld_max);
     if (P.has_trace) {
       HL_CUDA(cudaMemcpyAsync(&b_tr, P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
                               c->stream));
@@ -156,15 +148,7 @@ struct Solver {
 
   // trace-row entry of a residual vector from a device scalar
   void trace_fix(void* r, const void* src, const double* dscal, double add) {
-    if (o.precision == HALLAR_MIXED)
-      k_trace_fix<float><<<1, 32, 0, c->stream>>>((float*)r + (m - 1),
-                                                   src ? (const float*)src + (m - 1) : nullptr,
-                                                   dscal, add);
-    else
-      k_trace_fix<double><<<1, 32, 0, c->stream>>>((double*)r + (m - 1),
-                                                    src ? (const double*)src + (m - 1) : nullptr,
-                                                    dscal, add);
-    HL_CHECK_LAUNCH(c);
+    launch_trace_fix(c, r, src, dscal, add);
   }
   // the kernels' copy of p after p changed
   void refresh_pk() {
@@ -347,28 +331,13 @@ struct Solver {
 
   void trim_rank() {
     // keep the r_cap leading eigenvectors of Y^T Y (Y = Ytil, rank columns)
-    const int r = rank, k = o.r_cap;
-    launch_gram(c, Ytil, ld, r, gram);
-    std::vector<double> G((size_t)r * r), V, w;
-    HL_CUDA(cudaMemcpyAsync(G.data(), gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                            c->stream));
-    sync(c);
-    jacobi_eig(G, r, V, w);
-    std::vector<int> idx(r);
-    for (int i = 0; i < r; ++i) idx[i] = i;
-    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
-    std::vector<double> Qk((size_t)r * k);
-    for (int a = 0; a < r; ++a)
-      for (int b = 0; b < k; ++b) Qk[(size_t)a * k + b] = V[(size_t)a * r + idx[b]];
-    HL_CUDA(cudaMemcpyAsync(gram, Qk.data(), Qk.size() * sizeof(double), cudaMemcpyHostToDevice,
-                            c->stream));
+    const int k = o.r_cap;
     const int ld_new = padded_ld(c, k);
-    launch_right_mult(c, Ytil, ld, r, gram, k, tmp, ld_new);
+    trim_factor(c, Ytil, ld, rank, k, tmp, ld_new, nullptr);
     std::swap(Ytil, tmp);
     rank = k;
     ld = ld_new;
     R.trims++;
-    sync(c);
   }
 
   hallar_status run(const void* U0d, int r0, const double* p0d, hallar_result* out) {
@@ -516,6 +485,35 @@ struct Solver {
 };
 
 }  // namespace
+
+// Rank trim (not in the paper; the rank cap of hallar_options): out = Y Q_k
+// with Q_k the k leading eigenvectors of the Gram Y^T Y (FP64, cyclic
+// Jacobi on the host), so out out^T is the best rank-k approximation of
+// YY^T (Eckart-Young).  eigs (host, may be null) receives the r Gram
+// eigenvalues in descending order.
+void trim_factor(Ctx* c, const void* Y, int ld, int r, int k, void* out, int ld_out,
+                 double* eigs) {
+  double* gram = (double*)ensure_buffer(c, &c->trim_gram, &c->trim_gram_bytes,
+                                        (size_t)r * (r > k ? r : k) * sizeof(double));
+  launch_gram(c, Y, ld, r, gram);
+  std::vector<double> G((size_t)r * r), V, w;
+  HL_CUDA(cudaMemcpyAsync(G.data(), gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+  sync(c);
+  jacobi_eig(G, r, V, w);
+  std::vector<int> idx(r);
+  for (int i = 0; i < r; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return w[a] > w[b]; });
+  if (eigs)
+    for (int i = 0; i < r; ++i) eigs[i] = w[idx[i]];
+  std::vector<double> Qk((size_t)r * k, 0.0);
+  for (int a = 0; a < r; ++a)
+    for (int b = 0; b < k && b < r; ++b) Qk[(size_t)a * k + b] = V[(size_t)a * r + idx[b]];
+  HL_CUDA(cudaMemcpyAsync(gram, Qk.data(), Qk.size() * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+  launch_right_mult(c, Y, ld, r, gram, k, out, ld_out);
+  sync(c);
+}
 
 hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_result* res) {
   // the previous solve's buffers are released before a new solve allocates

@@ -24,9 +24,9 @@ HALLAR_FP64, HALLAR_MIXED = 0, 1
 FAMILY = {"diag": HALLAR_DIAG, "edge": HALLAR_EDGE, "observed": HALLAR_OBSERVED}
 
 EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_grad",
-            "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
+            "hallar_value_change", "hallar_trim_rank", "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
             "hallar_destroy", "hallar_last_error", "hallar_status_string", "hallar_profile",
-            "hallar_grad_diag_noalloc", "hallar_solve_footprint", "hallar_server_create",
+            "hallar_profile_sampling", "hallar_grad_diag_noalloc", "hallar_solve_footprint", "hallar_server_create",
             "hallar_server_submit", "hallar_server_wait", "hallar_server_get_stats",
             "hallar_server_destroy", "hallar_server_last_error", "hallar_batch_create",
             "hallar_batch_layout", "hallar_batch_grad", "hallar_batch_shape",
@@ -98,11 +98,14 @@ def _load():
                            C.POINTER(C.c_void_p)], C.c_int),
         "hallar_eval_A": ([P, P, I32, P], C.c_int),
         "hallar_grad": ([P, P, I32, P, D, P, P, P], C.c_int),
+        "hallar_value_change": ([P, P, P, I32, P, D, P, P, P], C.c_int),
+        "hallar_trim_rank": ([P, P, I32, I32, P, P], C.c_int),
         "hallar_min_eig": ([P, P, D, I32, P, P, P, P, P], C.c_int),
         "hallar_solve": ([P, P, I32, P, P], C.c_int),
         "hallar_get_solution": ([P, P, I32, P, P], C.c_int),
         "hallar_get_sizes": ([P, P, P, P, P], C.c_int),
-        "hallar_profile": ([P, I32, P, P, P], C.c_int),
+        "hallar_profile": ([P, I32, P, P, P, P], C.c_int),
+        "hallar_profile_sampling": ([P, I32], C.c_int),
         "hallar_grad_diag_noalloc": ([I64, I32, P, P, P, P, P, P, D, P, P, P, P, P, C.c_char_p,
                                       I32], C.c_int),
         "hallar_solve_footprint": ([P], I64),
@@ -227,6 +230,19 @@ def hallar_grad(h, U, r, p, beta, W, resid=None):
     return g.value
 
 
+def hallar_value_change(h, X, Y, r, p, beta, rX=None, rY=None):
+    """Returns g(Y) - g(X); rY (if given) receives A(YY^T) - b."""
+    dg = C.c_double()
+    _check(_lib.hallar_value_change(h, _ptr(X), _ptr(Y), int(r), _ptr(p), float(beta), _ptr(rX),
+                                    C.byref(dg), _ptr(rY)), h)
+    return dg.value
+
+
+def hallar_trim_rank(h, Y, r, k, Yout, eigs=None):
+    """Yout = Y Q_k (k leading Gram eigenvectors); eigs (host float64 [r]) optional."""
+    return _check(_lib.hallar_trim_rank(h, _ptr(Y), int(r), int(k), _ptr(Yout), _ptr(eigs)), h)
+
+
 def hallar_min_eig(h, pshift, tol, kmax, v0=None, v=None):
     """Returns (lambda_min, iterations, residual, converged)."""
     lam = C.c_double()
@@ -260,15 +276,23 @@ def hallar_get_sizes(h):
     return n.value, m.value, nnz.value, prec.value
 
 
-def hallar_profile(h, op):
+def hallar_profile(h, op, padded=False):
     """op 1: clear and start kernel timing, 2: stop, 0: read.  Returns
     (ms[3], launches[3], bytes[3]) for the fused operator, value-change and
-    Lanczos kernel classes."""
+    Lanczos kernel classes, plus bytes_padded[3] when padded is true."""
     ms = (C.c_double * 3)()
     nl = (C.c_int64 * 3)()
     by = (C.c_double * 3)()
-    _check(_lib.hallar_profile(h, int(op), ms, nl, by), h)
+    bp = (C.c_double * 3)()
+    _check(_lib.hallar_profile(h, int(op), ms, nl, by, bp), h)
+    if padded:
+        return list(ms), list(nl), list(by), list(bp)
     return list(ms), list(nl), list(by)
+
+
+def hallar_profile_sampling(h, every):
+    """Time only every `every`-th launch of each kernel class."""
+    return _check(_lib.hallar_profile_sampling(h, int(every)), h)
 
 
 def hallar_grad_diag_noalloc(n, r, rowptr, col, cval, cdiag, b, p, beta, U, W, resid, g_out,

@@ -137,6 +137,29 @@ def test_full_size_torus_gradient(H):
         assert np.linalg.norm(res - ref.resid) <= TOL[prec] * np.linalg.norm(ref.T[1:])
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_full_size_theta_gnm_gradient(H, prec):
+    # the Lovasz theta workload at its full size: G(n, M) with n = 1e5 and
+    # M = 1e6 distinct edges, the trace row, implicit C = -11^T, r = 64
+    inst = I.theta_gnm(100_000, 1_000_000, seed=3)
+    rng = np.random.default_rng(6)
+    U = rng.standard_normal((inst.n, 64)) / 8.0
+    p = rng.standard_normal(inst.m)
+    g, W, res, Ueff = run_grad(H, inst, U, p, 2.0, prec)
+    ref = O.al_grad(inst, Ueff, p, 2.0)
+    tol = TOL[prec]
+    assert nrel(W, ref.W) <= tol
+    assert np.linalg.norm(res - ref.resid) <= tol * np.linalg.norm(ref.T[1:])
+    assert abs(g - ref.g) <= tol * scalar_scale(inst, Ueff, p, 2.0)
+    dt = np.float32 if prec else np.float64
+    with H.create_from_instance(inst, prec) as hd:
+        Td = torch.empty(inst.m + 1, dtype=torch.float64, device="cuda")
+        H.hallar_eval_A(hd.h, torch.from_numpy(U.astype(dt)).cuda(), 64, Td)
+        T = Td.cpu().numpy()
+    assert nrel(T[1:], ref.T[1:]) <= tol
+    assert abs(T[0] - ref.T[0]) <= tol * scalar_scale(inst, Ueff, np.zeros(inst.m), 0.0)
+
+
 def test_empty_rows_and_isolated_vertices(H):
     ei = np.array([0, 5, 9])
     ej = np.array([3, 7, 2])
