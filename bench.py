@@ -65,9 +65,12 @@ WORKLOADS = {
 
 
 def run_kernel(args):
-    """The fused constraint map + shift + SpMM alone (hallar_grad on device
-    arrays) on the workload's full-size instance: W + K launches, timed with
-    CUDA events on the launching stream; prints achieved GB/s."""
+    """One operator kernel alone on the workload's full-size instance, from
+    device arrays: --kernel grad times the fused constraint map + shift +
+    SpMM (hallar_grad), --kernel change the AL value change g(Y) - g(X)
+    (hallar_value_change, Y a small step from X).  W + K calls, each
+    launch timed with CUDA events on the launching stream; prints achieved
+    GB/s on the algorithmic bytes."""
     import torch
 
     from paper_2505_13719_b300 import hallar as H
@@ -85,19 +88,30 @@ def run_kernel(args):
     W = torch.empty_like(U)
     p = torch.randn(inst.m, device="cuda", dtype=torch.float64, generator=gen)
     res = torch.empty(inst.m, device="cuda", dtype=torch.float64)
+    if args.kernel == "grad":
+        cls, name = 0, "fused_constraint_map_shift_spmm"
+        call = lambda: H.hallar_grad(hd.h, U, r, p, 1.5, W, res)  # noqa: E731
+    else:
+        cls, name = 1, "value_change"
+        Y = (U.double() + 1e-3 * torch.randn(inst.n, r, device="cuda", dtype=torch.float64,
+                                             generator=gen)).to(tdt)
+        H.hallar_grad(hd.h, U, r, p, 1.5, W, res)  # r_X at X
+        rY = torch.empty_like(res)
+        call = lambda: H.hallar_value_change(hd.h, U, Y, r, p, 1.5, res, rY)  # noqa: E731
     for _ in range(args.warmup):
-        H.hallar_grad(hd.h, U, r, p, 1.5, W, res)
+        call()
     H.hallar_profile(hd.h, 1)
     for _ in range(args.steps):
-        H.hallar_grad(hd.h, U, r, p, 1.5, W, res)
-    ms, nl, by = H.hallar_profile(hd.h, 2)
+        call()
+    ms, nl, by, bp = H.hallar_profile(hd.h, 2, padded=True)
     hd.close()
     peaks = load_peaks()
-    gbs = by[0] / (ms[0] / 1e3) / 1e9
-    return {"kernel": "fused_constraint_map_shift_spmm", "workload": wl["desc"],
-            "precision": args.precision, "rank": r, "launches": nl[0],
-            "avg_launch_us": round(1e3 * ms[0] / nl[0], 2),
-            "bytes_per_launch": by[0] / nl[0], "achieved_GBps": round(gbs, 1),
+    gbs = by[cls] / (ms[cls] / 1e3) / 1e9
+    return {"kernel": name, "workload": wl["desc"],
+            "precision": args.precision, "rank": r, "launches": nl[cls],
+            "avg_launch_us": round(1e3 * ms[cls] / nl[cls], 2),
+            "bytes_per_launch": by[cls] / nl[cls],
+            "bytes_with_padding_per_launch": bp[cls] / nl[cls], "achieved_GBps": round(gbs, 1),
             "peak_GBps": peaks["hbm_gbs"], "frac": round(gbs / peaks["hbm_gbs"], 4)}
 
 
@@ -679,8 +693,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tol2", action="store_true",
                     help="skip the extra solve at KKT 5e-6 (objective check)")
-    ap.add_argument("--kernel", choices=["grad"], default=None,
-                    help="time the fused operator kernel alone instead of full solves")
+    ap.add_argument("--kernel", choices=["grad", "change"], default=None,
+                    help="time one operator kernel alone instead of full solves")
     ap.add_argument("--rank", type=int, default=10, help="factor width for --kernel")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: a Poisson stream of mixed solves through hallar_server")
