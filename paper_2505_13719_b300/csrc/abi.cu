@@ -53,8 +53,8 @@ double* pinned_scalars_acquire() {
   std::lock_guard<std::mutex> lock(g_pin_mu);
   if (g_pin_free.empty()) {
     double* slab = nullptr;
-    HL_CUDA(cudaMallocHost((void**)&slab, (size_t)kPinSlab * S_COUNT * sizeof(double)));
-    for (int i = kPinSlab - 1; i >= 0; --i) g_pin_free.push_back(slab + (size_t)i * S_COUNT);
+    HL_CUDA(cudaMallocHost((void**)&slab, (size_t)kPinSlab * kPinDoubles * sizeof(double)));
+    for (int i = kPinSlab - 1; i >= 0; --i) g_pin_free.push_back(slab + (size_t)i * kPinDoubles);
   }
   double* p = g_pin_free.back();
   g_pin_free.pop_back();
@@ -89,7 +89,7 @@ void fetch_scalars(Ctx* c, int first, int count) {
 }
 
 int prof_begin(Ctx* c, int cls, OpBytes bytes) {
-  if (!c->prof_on) return -1;
+  if (!c->prof_on || c->capturing) return -1;
   if (c->prof_seen[cls]++ % c->prof_every != 0) return -1;  // not sampled
   c->prof_bytes[cls] += bytes.alg;
   c->prof_bytes_pad[cls] += bytes.pad;
@@ -711,7 +711,7 @@ hallar_status hallar_value_change(hallar_t h, const void* X, const void* Y, int3
     if (mixed && ryk) launch_to_double(c, m, ryd, ryk);
     fetch_scalars(c, 0, S_COUNT);
     const double* hs = c->h_scal;
-    const double dT0 = hs[S_DIFF] + (c->P.C_J != 0.0 ? c->P.C_J * hs[S_DIFF + 5] : 0.0);
+    const double dT0 = hs[S_DIFF] + (c->P.C_J != 0.0 ? c->P.C_J * hs[S_DIFF + 9] : 0.0);
     double pdT = hs[S_DIFF + 1], q = hs[S_DIFF + 2];
     if (c->P.has_trace) {
       double pt = 0.0, rxt = 0.0;

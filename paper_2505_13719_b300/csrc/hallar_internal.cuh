@@ -81,11 +81,94 @@ struct OpBytes {
   double alg = 0.0, pad = 0.0;
 };
 
+// ---------------------------------------------------------------------------
+// arguments of the operator kernels that the device-side ADAP-AIPP loop
+// (loop.cu) rewrites between launches; an entry point passes them by value
+// ---------------------------------------------------------------------------
+// epilogue of the fused operator (kernels_ops.cu)
+enum GradEpi : int { EPI_W = 0, EPI_FISTA_Z = 1, EPI_AIPP = 2 };
+struct GradInd {
+  const void* U = nullptr;     // factor in
+  void* out = nullptr;         // W (EPI_W, may be null) or z (EPI_FISTA_Z)
+  void* resid = nullptr;       // residuals out (factor type), or null
+  const void* ctr = nullptr;   // prox centre (EPI_FISTA_Z, EPI_AIPP)
+  const void* zin = nullptr;   // unprojected step of the accepted y (EPI_AIPP)
+  double beta = 0.0, c2lam = 0.0, invL = 0.0, L = 0.0;
+  int active = 1, pad = 0;
+};
+struct VcInd {                 // value change g(Y) - g(X)
+  const void* X = nullptr;
+  const void* Y = nullptr;     // Y, or Z when Y = cs Z (ADAP-FISTA trial)
+  const void* rX = nullptr;    // residuals at X (factor type)
+  void* rY = nullptr;          // residuals at Y out, or null
+  const void* ctr = nullptr;   // prox centre (Y = cs Z form)
+  void* y_out = nullptr;       // Y = cs Z out (Y = cs Z form)
+  int active = 1, pad = 0;
+};
+struct ColInd {                // column-sum pre-passes
+  const void* U = nullptr;     // factor (mode 0) or X (mode 1)
+  const void* Y = nullptr;     // mode 1: Y, or Z when y_from_z
+  int active = 1, y_from_z = 0;
+};
+struct TraceInd {              // trace-row residual entry
+  void* dst = nullptr;
+  int active = 1, pad = 0;
+};
+struct XInd {                  // ADAP-FISTA x and x~ updates
+  void* x = nullptr;           // x out
+  const void* x_src = nullptr; // x in (the centre on the first update)
+  void* xt = nullptr;          // x~ out
+  const void* xt_src = nullptr;// x~ in (mode 1)
+  const void* y = nullptr;
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, w0 = 0.0, w1 = 0.0;
+  int mode = 0, active = 0;    // mode 0: x~ = w0 y + w1 x; mode 1: step 3's x
+                               // update, then x~ = w0 y + w1 x
+};
+
+// Device-resident state of one ADAP-AIPP call (Appendix A) and of its
+// ADAP-FISTA calls (Appendix A.1).  The host fills the fixed part and the
+// evolving part's start values, launches the loop (as a CUDA graph of two
+// nested WHILE nodes, or kernel by kernel), and reads the results back.
+// Factor buffers rotate by index: pool[i_ctr] is the prox centre, pool[i_y]
+// the current ADAP-FISTA y and pool[i_ynew] the trial's y; x, x~ and z have
+// buffers of their own (x and x~ are the centre until first written).
+struct LoopCtl {
+  void* pool[3];
+  void* xb;
+  void* xtb;
+  void* zb;
+  void* rpool[2];              // residuals at the centre / at the accepted y
+  void* rX;                    // residuals at x~
+  int i_ctr, i_y, i_ynew, i_rctr;
+  int x_alias, xt_alias, mixed, has_trace;
+  // fixed for the call
+  double beta, tau, chi, sigma, mu, slack_u, rho, C_J, b_tr, p_tr;
+  int max_fista, max_aipp, attempt_cap, trial_cap;
+  // evolving
+  double lam, Mbar, nrm_ctr2;
+  double A, tk, L, Ln, a, Lacc;
+  int fista_it, fista_status, trials, aipp_j;
+  int done, attempts, error, graph_mode;
+  // operator scalars at the accepted W (valid when done)
+  double gT0, gpr, grr, gmag, gnrm2, gWU, Rn;
+  // counters since the call started
+  long long n_fista_iters, n_fista_fail, n_aipp_iters, n_grads, n_values, n_trials, n_attempts;
+  unsigned long long h_fista, h_aipp;  // cudaGraphConditionalHandle of the two loops
+  int cont_fista, cont_aipp;           // loop conditions (read by the host in kernel-by-kernel mode)
+  // kernel argument blocks
+  GradInd g_trial, g_check;
+  VcInd v_trial, v_check;
+  ColInd c_trial, c_check, cd_trial, cd_check;
+  TraceInd t_trial, t_check;
+  XInd xi;
+};
+
 // device scalar slots (doubles), mirrored to pinned host memory
 enum Slot : int {
-  S_GRAD = 0,    // fused operator: C.UU^T part, p.r, r.r
+  S_GRAD = 0,    // fused operator: C.UU^T part, p.r, r.r, magnitude, epilogue sums [4..7]
   S_PRE = 8,     // pre-pass: |U|_F^2, |colsum|^2
-  S_DIFF = 16,   // value change: dT0, p.dT, dT(2rX+dT), trace dT; [4..5] colsum pass
+  S_DIFF = 16,   // value change: dT0, p.dT, dT(2rX+dT), trace dT, [4..6] prox sums;
+                 // [8..9] colsum-difference pass
   S_VEC = 32,    // streaming kernels
   S_VEC2 = 48,   // streaming kernels (second set)
   S_LAN = 64,    // Lanczos
@@ -132,6 +215,7 @@ struct hallar_ctx {
   void* lan_h = nullptr; size_t lan_h_bytes = 0;
   // kernel timing (hallar_profile): event pairs pending per kernel class
   bool prof_on = false;
+  bool capturing = false;             // kernels are being captured into a graph
   int prof_every = 1;                 // time every prof_every-th launch of a class
   int64_t prof_seen[3] = {0, 0, 0};   // launches of each class since the last clear
   double prof_ms[3] = {0.0, 0.0, 0.0};
@@ -188,8 +272,11 @@ T* dalloc(Ctx* c, size_t count) {
   c->owned.push_back(p);
   return static_cast<T*>(p);
 }
-// pinned blocks of S_COUNT doubles for the scalar read-backs, recycled across
-// handles (cudaFreeHost would synchronise the device)
+// pinned blocks for the scalar read-backs (S_COUNT doubles) and the host
+// mirror of a solve's LoopCtl, recycled across handles (cudaFreeHost would
+// synchronise the device)
+constexpr int kPinDoubles = S_COUNT + 256;
+static_assert(sizeof(LoopCtl) <= 256 * sizeof(double), "LoopCtl outgrew its pinned mirror");
 double* pinned_scalars_acquire();
 void pinned_scalars_release(double* p);
 void dfree(Ctx* c, void* p);
@@ -237,14 +324,26 @@ inline void* cj_row(const Ctx* c) { return c->d_colsum + 3 * kColsumMax; }
 // p has the factor's element type (float copy in the mixed form)
 void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
                  GradOut out);
+// the fused operator with the ADAP-FISTA (EPI_FISTA_Z: S_GRAD[4..6] = |z|^2,
+// <g, x~>, |g|^2) or ADAP-AIPP (EPI_AIPP: S_GRAD[4..7] = <V, D>, |D|^2,
+// |V - D|^2, <W, y>) epilogue, its arguments read from device memory
+void launch_grad_epi(Ctx* c, int epi, int ld, int r, const void* p, const GradInd* gind);
 // g(Y) - g(X) pieces into S_DIFF: [0] dT0 (no C_J part) [1] p.dT [2] dT(2rX+dT)
 // [3] trace dT = sum <D_i, Y_i + X_i>; rY (if non-null) = rX + dT.
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r,
                          const void* p, const void* rX, void* rY);
+// the same with arguments from device memory; y_from_z: Y = cs Z (cs from
+// S_GRAD[4] = |Z|^2 and tau), Y stored, and S_DIFF[4..6] = |Y - X|^2,
+// <Y - X, (Y + X)/2 - centre>, |Y - centre|^2
+void launch_value_change_ind(Ctx* c, bool y_from_z, int ld, int r, const void* p,
+                             const VcInd* vind);
 // colsum of D = Y - X and of Y + X (for the C_J part of a value change);
-// S_DIFF[4] = sum <D_i, Y_i + X_i>, S_DIFF[5] = <colsum D, colsum (Y + X)>
+// S_DIFF[8] = sum <D_i, Y_i + X_i>, S_DIFF[9] = <colsum D, colsum (Y + X)>
 void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD,
                         double* sS);
+// the column-sum pre-passes with arguments from device memory
+void launch_colsum_ind(Ctx* c, int ld, const ColInd* cind);
+void launch_colsum_diff_ind(Ctx* c, int ld, const ColInd* cind);
 
 // r = 1 operator pieces in FP64 (Frank-Wolfe)
 void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, int slot);
@@ -252,21 +351,8 @@ void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, in
 // streaming kernels (kernels_vec.cu); reductions into the given slot
 void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst, int r_copy,
                      double scale_src);
-void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, double a,
-                     int ld);
-// ADAP-FISTA step 3's x update, x <- [mu a y + tk x - a (L - mu)(xt - y)] / tk_new,
-// and in the same pass the next first trial's x~ = (A_next y + a_next x) / (A_next + a_next)
-void launch_fista_x_xt(Ctx* c, void* x, const void* y, void* xt, double mu, double a,
-                       double tk, double tk_new, double L, double A_next, double a_next, int ld);
-void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,
-                    double lam, double L, int ld);
-void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* center,
-                    const void* W, double lam, double tau, int ld);
-void launch_aipp_check(Ctx* c, const void* Wy, const void* z, const void* y,
-                       const void* center, double lam, double L, int ld);
 void launch_scale(Ctx* c, void* U, int ld, double s);
 void launch_norm2(Ctx* c, const void* U, int ld, int slot);
-void launch_dot(Ctx* c, const void* W, const void* U, int ld, int slot);
 void launch_fw_append(Ctx* c, const void* Y, int ld, int r, const double* y, double sY,
                       double sy, void* Ynew, int ld_new, int append);
 // m-length FP64 vectors: op 0: a = b + s cc; op 1: slot = <b, cc>; op 2: slot = |b|^2
@@ -297,6 +383,14 @@ void launch_splitmix(Ctx* c, uint64_t seed, double* out, double mix_scale, const
 // trace-row entry of a residual vector (factor type) from a device scalar:
 // r[m-1] = (src ? src[m-1] : 0) + *dscal + add
 void launch_trace_fix(Ctx* c, void* r, const void* src, const double* dscal, double add);
+
+// device-side ADAP-AIPP / ADAP-FISTA control (loop.cu)
+void launch_loop_reset(Ctx* c, LoopCtl* L);        // attempts = 0 (top of a graph launch)
+void launch_aipp_begin(Ctx* c, LoopCtl* L);        // start an ADAP-FISTA call
+void launch_fista_ctl(Ctx* c, LoopCtl* L);         // ADAP-FISTA steps 2-5 after a trial
+void launch_aipp_ctl(Ctx* c, LoopCtl* L);          // ADAP-AIPP steps 2-3 after a call
+void launch_loop_x(Ctx* c, int ld, LoopCtl* L);    // x / x~ updates (XInd of L)
+void launch_trace_fix_ind(Ctx* c, const TraceInd* ti, double add);  // dst[m-1] = S_PRE[0] + add
 
 // solver (solver.cu)
 hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_result* res);

@@ -15,12 +15,24 @@
 // (ld.global.nc): on mesh-like graphs neighbours i +- 1 are rows of the same
 // warp or block, and the rest of the gather window of a row-ordered sweep
 // sits in the 126 MB L2.
+#include <cmath>
+
 #include "device_common.cuh"
 #include "hallar_internal.cuh"
 
 namespace hallar {
 
 namespace {
+
+// Resident blocks per SM the register allocation must allow, for the float
+// diagonal-family kernels with one thread per row of up to three 16-byte
+// chunks (Max-Cut in the mixed form): each thread keeps one row's gathers in
+// flight, so more warps hide more latency.  `want` is 4 (64 registers) for
+// the plain passes and 3 (80 registers) for the variants with the most live
+// sums; every other shape keeps the compiler's own register count.
+template <class T, int FAM, int G, int K, int want>
+constexpr int kMinBlocks =
+    (sizeof(T) == 4 && FAM == FAM_DIAG && G == 1 && K <= 3) ? want : 1;
 
 // edges whose metadata one group loads at once (at most the group's lanes)
 template <int G>
@@ -60,45 +72,65 @@ struct OpArgs {
 // fused constraint map + shift + SpMM
 // ---------------------------------------------------------------------------
 struct GradIO {
-  const void* __restrict__ U;
   const void* __restrict__ cjv;       // T[ld] or null: C_J 11^T U = 1 (C_J colsum)^T
   const double* __restrict__ pre;     // pre[0] = |U|_F^2 (trace row)
-  void* __restrict__ W;               // T, or null
-  void* __restrict__ resid;           // T, or null
   void* __restrict__ Tout;            // T: A_l . UU^T at [l], or null
 };
 
+// Epilogues of the row pass (what the kernel does with W_i = (C + A*(p'))_i U
+// once row i is complete; W itself is formed in registers):
+//   EPI_W        store W (hallar_grad, the outer loop)
+//   EPI_FISTA_Z  ADAP-FISTA step 2's unprojected step at U = x~ (Appendix A.1):
+//                g = grad psi_s(x~) = 2 lam W + x~ - centre, z = x~ - g / L;
+//                store z; reduce |z|^2, <g, x~>, |g|^2 (the ball projection
+//                y = min(1, tau/|z|) z and <g, y - x~> follow from these)
+//   EPI_AIPP     ADAP-AIPP step 2 at U = y (z its unprojected step):
+//                V - D = 2 lam W + L (z - y), D = y - centre; reduce <V, D>,
+//                |D|^2, |V - D|^2 (R_j = (V - D)/lam, eq. Rj def) and <W, y>
+//                (G . YY^T of the gap test); W is not stored
+// The pointers and coefficients come from a GradInd, by value or (when the
+// device-side ADAP-AIPP loop fills it) from device memory.
+template <int EPI>
+constexpr int kGradRed = EPI == EPI_W ? 4 : (EPI == EPI_FISTA_Z ? 7 : 8);
+
 // CJ: C has the implicit C_J 11^T part (a compile-time switch: an unused
 // runtime branch would still cost predicated instructions in the row loop)
-template <class T, int FAM, int G, int K, bool CJ>
-__global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
+template <class T, int FAM, int G, int K, bool CJ, int EPI>
+__global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AIPP ? 3 : 4>) k_grad(OpArgs a, GradIO io, GradInd gi,
+                                                 const GradInd* __restrict__ gind) {
   using Tr = FamTraits<FAM>;
   constexpr int VEC = V16<T>::N;
-  const T* __restrict__ U = static_cast<const T*>(io.U);
+  if (gind != nullptr) gi = *gind;
+  if (!gi.active) return;  // uniform over the grid: no block reaches the reduction
+  const T* __restrict__ U = static_cast<const T*>(gi.U);
   const T* __restrict__ cval = static_cast<const T*>(a.cval);
   const T* __restrict__ cdiag = static_cast<const T*>(a.cdiag);
   const T* __restrict__ bv = static_cast<const T*>(a.b);
   const T* __restrict__ pv = static_cast<const T*>(a.p);
-  T* __restrict__ W = static_cast<T*>(io.W);
-  T* __restrict__ resid = static_cast<T*>(io.resid);
+  T* __restrict__ W = static_cast<T*>(gi.out);
+  T* __restrict__ resid = static_cast<T*>(gi.resid);
   T* __restrict__ Tout = static_cast<T*>(io.Tout);
   const T* __restrict__ cjv = static_cast<const T*>(io.cjv);
+  const T* __restrict__ ctr = static_cast<const T*>(gi.ctr);
+  const T* __restrict__ zin = static_cast<const T*>(gi.zin);
   const int lane_g = threadIdx.x & (G - 1);
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
   const int nch = a.ld / VEC;
-  const T beta = (T)a.beta;
+  const T beta = (T)gi.beta;
+  const T c2lam = (T)gi.c2lam, invL = (T)gi.invL, Lt = (T)gi.L;
 
   // shifted multiplier of the trace row, identical for every row
   T ps_tr = (T)0;
   if (Tr::kPairs && a.has_trace) {
     const double rt = io.pre[0] - (double)bv[a.trace_row];
-    ps_tr = (T)((double)pv[a.trace_row] + a.beta * rt);
+    ps_tr = (T)((double)pv[a.trace_row] + gi.beta * rt);
   }
 
   // C.UU^T (sparse + diagonal part), p.r, r.r, and the magnitude
-  // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g
-  Acc<T> acc_t0, acc_pr, acc_rr, acc_mag;
+  // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g;
+  // e0..e3: the epilogue's sums
+  Acc<T> acc_t0, acc_pr, acc_rr, acc_mag, e0s, e1s, e2s, e3s;
   for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
     T u[K][VEC], acc[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
@@ -227,47 +259,99 @@ __global__ void __launch_bounds__(kBlock) k_grad(OpArgs a, GradIO io) {
       acc_mag.add(tabs(cdi) * nrm);
     }
 
-    if (W != nullptr) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int ch = lane_g + k * G;
-        if (ch < nch) {
-          T w[VEC];
+    for (int k = 0; k < K; ++k) {
+      const int ch = lane_g + k * G;
+      if (ch >= nch) continue;
+      T w[VEC];
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) w[v] = tfma(dcoef, u[k][v], acc[k][v]);
-          if constexpr (CJ) {
-            // the C_J 11^T U term adds C_J * colsum to every row of W
+      for (int v = 0; v < VEC; ++v) w[v] = tfma(dcoef, u[k][v], acc[k][v]);
+      if constexpr (CJ) {
+        // the C_J 11^T U term adds C_J * colsum to every row of W
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) w[v] += __ldg(&cjv[ch * VEC + v]);
-          }
-          store_chunk<T>(W, rowoff + ch * VEC, w);
+        for (int v = 0; v < VEC; ++v) w[v] += __ldg(&cjv[ch * VEC + v]);
+      }
+      if constexpr (EPI == EPI_W) {
+        if (W != nullptr) store_chunk<T>(W, rowoff + ch * VEC, w);
+      } else if constexpr (EPI == EPI_FISTA_Z) {
+        T cc[VEC], zz[VEC];
+        load_chunk<T>(ctr, rowoff + ch * VEC, cc);
+        T sz = (T)0, sgx = (T)0, sgg = (T)0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const T g = tfma(c2lam, w[v], u[k][v] - cc[v]);
+          zz[v] = tfma(-invL, g, u[k][v]);
+          sz = tfma(zz[v], zz[v], sz);
+          sgx = tfma(g, u[k][v], sgx);
+          sgg = tfma(g, g, sgg);
         }
+        store_chunk<T>(W, rowoff + ch * VEC, zz);
+        e0s.add(sz);
+        e1s.add(sgx);
+        e2s.add(sgg);
+      } else {
+        T cc[VEC], zz[VEC];
+        load_chunk<T>(ctr, rowoff + ch * VEC, cc);
+        load_chunk<T>(zin, rowoff + ch * VEC, zz);
+        T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const T D = u[k][v] - cc[v];
+          const T VmD = tfma(c2lam, w[v], Lt * (zz[v] - u[k][v]));
+          s0 = tfma(VmD + D, D, s0);
+          s1 = tfma(D, D, s1);
+          s2 = tfma(VmD, VmD, s2);
+          s3 = tfma(w[v], u[k][v], s3);
+        }
+        e0s.add(s0);
+        e1s.add(s1);
+        e2s.add(s2);
+        e3s.add(s3);
       }
     }
   }
-  Acc<T> red[4] = {acc_t0, acc_pr, acc_rr, acc_mag};
-  grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
+  if constexpr (EPI == EPI_W) {
+    Acc<T> red[4] = {acc_t0, acc_pr, acc_rr, acc_mag};
+    grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
+  } else if constexpr (EPI == EPI_FISTA_Z) {
+    Acc<T> red[7] = {acc_t0, acc_pr, acc_rr, acc_mag, e0s, e1s, e2s};
+    grid_reduce_acc<T, 7>(red, a.partials, a.counter, a.out);
+  } else {
+    Acc<T> red[8] = {acc_t0, acc_pr, acc_rr, acc_mag, e0s, e1s, e2s, e3s};
+    grid_reduce_acc<T, 8>(red, a.partials, a.counter, a.out);
+  }
 }
 
 // ---------------------------------------------------------------------------
 // g(Y) - g(X) without cancellation: every pair product difference is
 // <Y_a,Y_b> - <X_a,X_b> = <D_a, Y_b> + <X_a, D_b>, D = Y - X.
+// YZ: Y = cs Z with cs = min(1, tau/|Z|_F) read from the device (ADAP-FISTA
+// step 2's projection onto the ball B_tau, eq. dimensional ball), formed in
+// registers for the own row and every gathered neighbour and stored once;
+// the pass then also reduces |Y - X|^2, <Y - X, (Y + X)/2 - centre> and
+// |Y - centre|^2 (the prox terms of psi_s and step 4's |y - x_0|^2).
 // ---------------------------------------------------------------------------
 struct DiffIO {
-  const void* __restrict__ X;
-  const void* __restrict__ Y;
-  const void* __restrict__ rX;  // T
-  void* __restrict__ rY;        // T, or null
+  const double* __restrict__ z2;  // YZ: |Z|_F^2 on the device
+  double tau;                     // YZ: the ball radius
 };
 
-template <class T, int FAM, int G, int K>
-__global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
+template <bool YZ>
+constexpr int kDiffRed = YZ ? 7 : 4;
+
+template <class T, int FAM, int G, int K, bool YZ>
+__global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) k_value_change(OpArgs a, DiffIO io, VcInd vi,
+                                                         const VcInd* __restrict__ vind) {
   using Tr = FamTraits<FAM>;
   constexpr int VEC = V16<T>::N;
-  const T* __restrict__ X = static_cast<const T*>(io.X);
-  const T* __restrict__ Y = static_cast<const T*>(io.Y);
-  const T* __restrict__ rXv = static_cast<const T*>(io.rX);
-  T* __restrict__ rYv = static_cast<T*>(io.rY);
+  if (vind != nullptr) vi = *vind;
+  if (!vi.active) return;  // uniform over the grid
+  const T* __restrict__ X = static_cast<const T*>(vi.X);
+  const T* __restrict__ Yv = static_cast<const T*>(vi.Y);
+  const T* __restrict__ rXv = static_cast<const T*>(vi.rX);
+  T* __restrict__ rYv = static_cast<T*>(vi.rY);
+  const T* __restrict__ ctr = static_cast<const T*>(vi.ctr);
+  T* __restrict__ yout = static_cast<T*>(vi.y_out);
   const T* __restrict__ cval = static_cast<const T*>(a.cval);
   const T* __restrict__ cdiag = static_cast<const T*>(a.cdiag);
   const T* __restrict__ pv = static_cast<const T*>(a.p);
@@ -275,9 +359,15 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
   const int nch = a.ld / VEC;
+  T cs = (T)1;
+  if constexpr (YZ) {
+    const double zn = sqrt(*io.z2);
+    cs = (T)(zn > io.tau ? io.tau / zn : 1.0);
+  }
 
-  // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT
-  Acc<T> acc_t0, acc_pd, acc_q, acc_tr;
+  // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT; YZ:
+  // |D|^2, <D, (Y + X)/2 - centre>, |Y - centre|^2
+  Acc<T> acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s;
   for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
     T x[K][VEC], d[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
@@ -287,7 +377,26 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
       T y[VEC];
       if (ch < nch) {
         load_chunk<T>(X, rowoff + ch * VEC, x[k]);
-        load_chunk<T>(Y, rowoff + ch * VEC, y);
+        load_chunk<T>(Yv, rowoff + ch * VEC, y);
+        if constexpr (YZ) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) y[v] = cs * y[v];
+          T cc[VEC];
+          load_chunk<T>(ctr, rowoff + ch * VEC, cc);
+          store_chunk<T>(yout, rowoff + ch * VEC, y);
+          T s0 = (T)0, s1 = (T)0, s2 = (T)0;
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const T dd = y[v] - x[k][v];
+            const T yc = y[v] - cc[v];
+            s0 = tfma(dd, dd, s0);
+            s1 = tfma(dd, (T)0.5 * (y[v] + x[k][v]) - cc[v], s1);
+            s2 = tfma(yc, yc, s2);
+          }
+          e0s.add(s0);
+          e1s.add(s1);
+          e2s.add(s2);
+        }
       } else {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) x[k][v] = y[v] = (T)0;
@@ -341,7 +450,11 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
           if (ch < nch) {
             T xj[VEC], yj[VEC];
             load_chunk<T>(X, j * a.ld + ch * VEC, xj);
-            load_chunk<T>(Y, j * a.ld + ch * VEC, yj);
+            load_chunk<T>(Yv, j * a.ld + ch * VEC, yj);
+            if constexpr (YZ) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) yj[v] = cs * yj[v];
+            }
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
               pd = tfma(d[k][v], yj[v], pd);
@@ -365,8 +478,13 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
     }
     acc_t0.add(cd_l);
   }
-  Acc<T> red[4] = {acc_t0, acc_pd, acc_q, acc_tr};
-  grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
+  if constexpr (YZ) {
+    Acc<T> red[7] = {acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s};
+    grid_reduce_acc<T, 7>(red, a.partials, a.counter, a.out);
+  } else {
+    Acc<T> red[4] = {acc_t0, acc_pd, acc_q, acc_tr};
+    grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,16 +493,33 @@ __global__ void __launch_bounds__(kBlock) k_value_change(OpArgs a, DiffIO io) {
 // Thread t of a block owns column t mod ld of every (256 / ld)-th row; the
 // per-thread sums are combined per column in a fixed order, so each block's
 // partial row and the last block's total are deterministic.
+// With cind (device memory, filled by the device-side ADAP-AIPP loop) U and Y
+// come from there, an inactive cind makes the launch a no-op, and
+// y_from_z reads Y as cs Z, cs = min(1, tau/sqrt(*z2)) (ADAP-FISTA's ball
+// projection).
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int64_t n, int ld,
                                                    int mode, const T* __restrict__ Y,
                                                    double* partials, unsigned* counter,
                                                    double* colsum_out, double* colsum_out2,
                                                    double* scal_out, double cj,
-                                                   T* __restrict__ cj_out) {
+                                                   T* __restrict__ cj_out,
+                                                   const ColInd* __restrict__ cind,
+                                                   const double* __restrict__ z2, double tau) {
   // mode 0: s = colsum(U), scal = [|U|_F^2, |s|^2]
   // mode 1: X = U, D = Y - X: s = colsum(D), s2 = colsum(Y + X),
   //         scal = [sum <D_i, Y_i + X_i>, <s, s2>]
+  T ys = (T)1;
+  if (cind != nullptr) {
+    const ColInd ci = *cind;
+    if (!ci.active) return;  // uniform over the grid
+    U = static_cast<const T*>(ci.U);
+    Y = static_cast<const T*>(ci.Y);
+    if (ci.y_from_z) {
+      const double zn = sqrt(*z2);
+      ys = (T)(zn > tau ? tau / zn : 1.0);
+    }
+  }
   __shared__ double t1[kBlock], t2[kBlock];
   __shared__ double sh[kColsumMax], sh2[kColsumMax];
   __shared__ double shr[1][kBlock / 32];
@@ -401,7 +536,7 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
         acc.add(x);
         nrm.add(x * x);
       } else {
-        const T y = Y[i * ld + c];
+        const T y = ys * Y[i * ld + c];
         const T dd = y - x;
         acc.add(dd);
         acc2.add(y + x);
@@ -601,19 +736,50 @@ OpBytes op_bytes(const Ctx* c, int r, int ld, int factor_arrays, bool writes_res
   return o;
 }
 
+namespace {
+
+template <int EPI>
+void grad_dispatch(Ctx* c, const OpArgs& a, const GradIO& io, const GradInd& gi,
+                   const GradInd* gind, int ld) {
+  HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
+    if (io.cjv != nullptr) {
+      const int grid = wave_grid(c, k_grad<T, FAM, G, K, true, EPI>, a.n, kBlock / G, kBlock);
+      k_grad<T, FAM, G, K, true, EPI><<<grid, kBlock, 0, c->stream>>>(a, io, gi, gind);
+    } else {
+      const int grid = wave_grid(c, k_grad<T, FAM, G, K, false, EPI>, a.n, kBlock / G, kBlock);
+      k_grad<T, FAM, G, K, false, EPI><<<grid, kBlock, 0, c->stream>>>(a, io, gi, gind);
+    }
+  }));
+  HL_CHECK_LAUNCH(c);
+}
+
+template <bool YZ>
+void change_dispatch(Ctx* c, const OpArgs& a, const DiffIO& io, const VcInd& vi,
+                     const VcInd* vind, int ld) {
+  HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
+    const int grid = wave_grid(c, k_value_change<T, FAM, G, K, YZ>, a.n, kBlock / G, kBlock);
+    k_value_change<T, FAM, G, K, YZ><<<grid, kBlock, 0, c->stream>>>(a, io, vi, vind);
+  }));
+  HL_CHECK_LAUNCH(c);
+}
+
+}  // namespace
+
 void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
                  GradOut out) {
   if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
   OpArgs a = make_args(c, ld, S_GRAD);
   a.p = p;
-  a.beta = beta;
   const bool mixed = c->opt.precision == HALLAR_MIXED;
   GradIO io;
-  io.U = U;
   io.cjv = (c->P.C_J != 0.0) ? cj_row(c) : nullptr;
   io.pre = c->d_scal + S_PRE;
-  io.W = out.W;
-  io.resid = out.resid;
+  GradInd gi;
+  gi.U = U;
+  gi.out = out.W;
+  gi.resid = out.resid;
+  gi.beta = beta;
+  gi.active = 1;
   // constraint values leave the kernel in the factor type (no double
   // instructions in the row loop); the float form widens them afterwards
   void* tout = nullptr;
@@ -623,64 +789,115 @@ void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double bet
   io.Tout = tout;
   const int tok = prof_begin(c, 0, op_bytes(c, r, ld, out.W != nullptr ? 2 : 1,
                                             out.resid != nullptr, true, false));
-  HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
-    if (io.cjv != nullptr) {
-      const int grid = wave_grid(c, k_grad<T, FAM, G, K, true>, a.n, kBlock / G, kBlock);
-      k_grad<T, FAM, G, K, true><<<grid, kBlock, 0, c->stream>>>(a, io);
-    } else {
-      const int grid = wave_grid(c, k_grad<T, FAM, G, K, false>, a.n, kBlock / G, kBlock);
-      k_grad<T, FAM, G, K, false><<<grid, kBlock, 0, c->stream>>>(a, io);
-    }
-  }));
-  HL_CHECK_LAUNCH(c);
+  grad_dispatch<EPI_W>(c, a, io, gi, nullptr, ld);
   prof_end(c, tok);
   if (out.T && mixed) launch_to_double(c, c->P.m, out.T + 1, tout);
+}
+
+void launch_grad_epi(Ctx* c, int epi, int ld, int r, const void* p, const GradInd* gind) {
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  OpArgs a = make_args(c, ld, S_GRAD);
+  a.p = p;
+  GradIO io;
+  io.cjv = (c->P.C_J != 0.0) ? cj_row(c) : nullptr;
+  io.pre = c->d_scal + S_PRE;
+  io.Tout = nullptr;
+  const GradInd unused;
+  // factor arrays: x~, the centre and z out (FISTA); y, z and the centre (AIPP)
+  const int tok = prof_begin(c, 0, op_bytes(c, r, ld, 3, true, true, false));
+  if (epi == EPI_FISTA_Z) grad_dispatch<EPI_FISTA_Z>(c, a, io, unused, gind, ld);
+  else grad_dispatch<EPI_AIPP>(c, a, io, unused, gind, ld);
+  prof_end(c, tok);
 }
 
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r, const void* p,
                          const void* rX, void* rY) {
   OpArgs a = make_args(c, ld, S_DIFF);
   a.p = p;
-  DiffIO io{X, Y, rX, rY};
+  DiffIO io{nullptr, 0.0};
+  VcInd vi;
+  vi.X = X;
+  vi.Y = Y;
+  vi.rX = rX;
+  vi.rY = rY;
+  vi.active = 1;
   const int tok = prof_begin(c, 1, op_bytes(c, r, ld, 2, rY != nullptr, true, true));
-  HL_BY_FAM_TYPE(c, HL_BY_SHAPE(T, ld, {
-    const int grid = wave_grid(c, k_value_change<T, FAM, G, K>, a.n, kBlock / G, kBlock);
-    k_value_change<T, FAM, G, K><<<grid, kBlock, 0, c->stream>>>(a, io);
-  }));
-  HL_CHECK_LAUNCH(c);
+  change_dispatch<false>(c, a, io, vi, nullptr, ld);
   prof_end(c, tok);
 }
 
-void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot) {
-  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+void launch_value_change_ind(Ctx* c, bool y_from_z, int ld, int r, const void* p,
+                             const VcInd* vind) {
+  OpArgs a = make_args(c, ld, S_DIFF);
+  a.p = p;
+  DiffIO io{c->d_scal + S_GRAD + 4, std::sqrt(c->P.tau2)};
+  const VcInd unused;
+  if (y_from_z) {
+    // x~, z and the centre in, y out
+    const int tok = prof_begin(c, 1, op_bytes(c, r, ld, 4, false, true, true));
+    change_dispatch<true>(c, a, io, unused, vind, ld);
+    prof_end(c, tok);
+  } else {
+    const int tok = prof_begin(c, 1, op_bytes(c, r, ld, 2, false, true, true));
+    change_dispatch<false>(c, a, io, unused, vind, ld);
+    prof_end(c, tok);
+  }
+}
+
+namespace {
+template <class T>
+void colsum_launch(Ctx* c, const void* U, int ld, int mode, const void* Y, double* out1,
+                   double* out2, double* scal, void* cjo, const ColInd* cind) {
   const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
   const int grid = grid_for(c, c->P.n, rows_per_pass * 8);
-  const double cj = c->P.C_J;
-  void* cjo = cj != 0.0 ? cj_row(c) : nullptr;
-  if (c->opt.precision == HALLAR_MIXED)
-    k_colsum<float><<<grid, kBlock, 0, c->stream>>>(
-        (const float*)U, c->P.n, ld, 0, nullptr, c->red.partials, c->red.counter, colsum_out,
-        nullptr, c->d_scal + slot, cj, (float*)cjo);
-  else
-    k_colsum<double><<<grid, kBlock, 0, c->stream>>>(
-        (const double*)U, c->P.n, ld, 0, nullptr, c->red.partials, c->red.counter, colsum_out,
-        nullptr, c->d_scal + slot, cj, (double*)cjo);
+  k_colsum<T><<<grid, kBlock, 0, c->stream>>>(
+      (const T*)U, c->P.n, ld, mode, (const T*)Y, c->red.partials, c->red.counter, out1, out2,
+      scal, mode == 0 ? c->P.C_J : 0.0, (T*)cjo, cind, c->d_scal + S_GRAD + 4,
+      std::sqrt(c->P.tau2));
   HL_CHECK_LAUNCH(c);
+}
+}  // namespace
+
+void launch_colsum(Ctx* c, const void* U, int ld, double* colsum_out, int slot) {
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  void* cjo = c->P.C_J != 0.0 ? cj_row(c) : nullptr;
+  if (c->opt.precision == HALLAR_MIXED)
+    colsum_launch<float>(c, U, ld, 0, nullptr, colsum_out, nullptr, c->d_scal + slot, cjo,
+                         nullptr);
+  else
+    colsum_launch<double>(c, U, ld, 0, nullptr, colsum_out, nullptr, c->d_scal + slot, cjo,
+                          nullptr);
+}
+
+void launch_colsum_ind(Ctx* c, int ld, const ColInd* cind) {
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  void* cjo = c->P.C_J != 0.0 ? cj_row(c) : nullptr;
+  if (c->opt.precision == HALLAR_MIXED)
+    colsum_launch<float>(c, nullptr, ld, 0, nullptr, c->d_colsum, nullptr, c->d_scal + S_PRE,
+                         cjo, cind);
+  else
+    colsum_launch<double>(c, nullptr, ld, 0, nullptr, c->d_colsum, nullptr, c->d_scal + S_PRE,
+                          cjo, cind);
 }
 
 void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD, double* sS) {
   if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
-  const int rows_per_pass = kBlock / ld > 0 ? kBlock / ld : 1;
-  const int grid = grid_for(c, c->P.n, rows_per_pass * 8);
   if (c->opt.precision == HALLAR_MIXED)
-    k_colsum<float><<<grid, kBlock, 0, c->stream>>>(
-        (const float*)X, c->P.n, ld, 1, (const float*)Y, c->red.partials, c->red.counter, sD,
-        sS, c->d_scal + S_DIFF + 4, 0.0, nullptr);
+    colsum_launch<float>(c, X, ld, 1, Y, sD, sS, c->d_scal + S_DIFF + 8, nullptr, nullptr);
   else
-    k_colsum<double><<<grid, kBlock, 0, c->stream>>>(
-        (const double*)X, c->P.n, ld, 1, (const double*)Y, c->red.partials, c->red.counter, sD,
-        sS, c->d_scal + S_DIFF + 4, 0.0, nullptr);
-  HL_CHECK_LAUNCH(c);
+    colsum_launch<double>(c, X, ld, 1, Y, sD, sS, c->d_scal + S_DIFF + 8, nullptr, nullptr);
+}
+
+void launch_colsum_diff_ind(Ctx* c, int ld, const ColInd* cind) {
+  if (ld > kColsumMax) fail(HALLAR_EINVAL, "factor width above 256");
+  double* sD = c->d_colsum + kColsumMax;
+  double* sS = c->d_colsum + 2 * kColsumMax;
+  if (c->opt.precision == HALLAR_MIXED)
+    colsum_launch<float>(c, nullptr, ld, 1, nullptr, sD, sS, c->d_scal + S_DIFF + 8, nullptr,
+                         cind);
+  else
+    colsum_launch<double>(c, nullptr, ld, 1, nullptr, sD, sS, c->d_scal + S_DIFF + 8, nullptr,
+                          cind);
 }
 
 void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, int slot) {

@@ -1,9 +1,11 @@
-// Streaming kernels of ADAP-FISTA / ADAP-AIPP (Appendix A), the Frank-Wolfe
-// rank update (eq. tilde Y) and the rank trim.  Every kernel is one pass over
-// n x ld factor arrays with 16-byte vector accesses, and folds the Frobenius
-// norms and inner products the host needs into the same pass (FP64
-// accumulation, deterministic grid reduction).  Padding columns are zero and
-// every update here is linear, so they stay zero.
+// Streaming kernels: the start factor's ball projection, the Frank-Wolfe
+// rank update (eq. tilde Y), the rank trim and the m-vector operations of
+// the dual update.  Every factor kernel is one pass over n x ld arrays with
+// 16-byte vector accesses and folds the norms the host needs into the same
+// pass (deterministic grid reduction).  Padding columns are zero and every
+// update here is linear, so they stay zero.  (The ADAP-FISTA / ADAP-AIPP
+// vector steps are fused into the operator kernels, and the x / x~ updates
+// run in loop.cu.)
 #include "device_common.cuh"
 #include "hallar_internal.cuh"
 
@@ -42,134 +44,6 @@ struct OpBase {
   __device__ void setup() {}
 };
 
-// xt = (A y + a x) / (A + a)      (ADAP-FISTA step 2)
-template <class T>
-struct OpXt : OpBase {
-  T* xt; const T* y; const T* x; T wy, wx;
-  __device__ void operator()(int64_t v, Acc<T>*) const {
-    constexpr int VEC = V16<T>::N;
-    T a[VEC], b[VEC], o[VEC];
-    HL_LOAD(y, v, a);
-    HL_LOAD(x, v, b);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) o[k] = tfma(wy, a[k], wx * b[k]);
-    store_chunk<T>(xt, v * VEC, o);
-  }
-};
-
-// step 3's x update and, in the same pass, step 2's x~ of the next
-// iteration's first trial (whose stepsize L is the accepted one, so its
-// weights are known): x <- cy y + cx x + cxt xt, then xt <- wy y + wx x,
-// with the same arithmetic as OpX followed by OpXt
-template <class T>
-struct OpXXt : OpBase {
-  T* x; T* xt; const T* y; T cy, cx, cxt, wy, wx;
-  __device__ void operator()(int64_t v, Acc<T>*) const {
-    constexpr int VEC = V16<T>::N;
-    T a[VEC], b[VEC], t[VEC], o[VEC], q[VEC];
-    HL_LOAD(y, v, a);
-    HL_LOAD(x, v, b);
-    HL_LOAD(xt, v, t);
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      o[k] = tfma(cy, a[k], tfma(cx, b[k], cxt * t[k]));
-      q[k] = tfma(wy, a[k], wx * o[k]);
-    }
-    store_chunk<T>(x, v * VEC, o);
-    store_chunk<T>(xt, v * VEC, q);
-  }
-};
-
-// z = xt - grad psi_s(xt) / L with grad psi_s = 2 lam W + xt - center;
-// red[0] = |z|^2 (the ball projection is the scaling min(1, tau/|z|))
-template <class T>
-struct OpZ : OpBase {
-  T* z; const T* xt; const T* W; const T* ctr; T c2lam, invL;
-  __device__ void operator()(int64_t v, Acc<T>* red) const {
-    constexpr int VEC = V16<T>::N;
-    T a[VEC], w[VEC], cc[VEC], o[VEC];
-    HL_LOAD(xt, v, a);
-    HL_LOAD(W, v, w);
-    HL_LOAD(ctr, v, cc);
-    T s = (T)0;
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      const T g = tfma(c2lam, w[k], a[k] - cc[k]);
-      o[k] = tfma(-invL, g, a[k]);
-      s = tfma(o[k], o[k], s);
-    }
-    red[0].add(s);
-    store_chunk<T>(z, v * VEC, o);
-  }
-};
-
-// y = c z with c = min(1, tau/|z|) (|z|^2 read from the device); with
-// d = y - xt and g = grad psi_s(xt) = 2 lam W + xt - center:
-// red = [|d|^2, <g, d>, <d, (y + xt)/2 - center>, |y - center|^2]
-template <class T>
-struct OpY {
-  T* y; const T* z; const T* xt; const T* ctr; const T* W; const double* z2; double tau;
-  T c2lam;
-  T cs;
-  __device__ void setup() {
-    const double zn = sqrt(*z2);
-    cs = (T)(zn > tau ? tau / zn : 1.0);
-  }
-  __device__ void operator()(int64_t v, Acc<T>* red) const {
-    constexpr int VEC = V16<T>::N;
-    T zz[VEC], a[VEC], cc[VEC], w[VEC], o[VEC];
-    HL_LOAD(z, v, zz);
-    HL_LOAD(xt, v, a);
-    HL_LOAD(ctr, v, cc);
-    HL_LOAD(W, v, w);
-    T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      o[k] = cs * zz[k];
-      const T d = o[k] - a[k];
-      const T g = tfma(c2lam, w[k], a[k] - cc[k]);
-      const T yc = o[k] - cc[k];
-      s0 = tfma(d, d, s0);
-      s1 = tfma(g, d, s1);
-      s2 = tfma(d, (T)0.5 * (o[k] + a[k]) - cc[k], s2);
-      s3 = tfma(yc, yc, s3);
-    }
-    red[0].add(s0);
-    red[1].add(s1);
-    red[2].add(s2);
-    red[3].add(s3);
-    store_chunk<T>(y, v * VEC, o);
-  }
-};
-
-// ADAP-AIPP step 2-3 pieces at the FISTA output y (z its unprojected step):
-// V = 2 lam W(y) + (y - center) + L (z - y), D = y - center:
-// red = [<V, D>, |D|^2, |V - D|^2]   (R_j = (V - D) / lam, eq. Rj def)
-template <class T>
-struct OpAipp : OpBase {
-  const T* Wy; const T* z; const T* y; const T* ctr; T c2lam, L;
-  __device__ void operator()(int64_t v, Acc<T>* red) const {
-    constexpr int VEC = V16<T>::N;
-    T w[VEC], zz[VEC], yy[VEC], cc[VEC];
-    HL_LOAD(Wy, v, w);
-    HL_LOAD(z, v, zz);
-    HL_LOAD(y, v, yy);
-    HL_LOAD(ctr, v, cc);
-    T s0 = (T)0, s1 = (T)0, s2 = (T)0;
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) {
-      const T D = yy[k] - cc[k];
-      const T VmD = tfma(c2lam, w[k], L * (zz[k] - yy[k]));
-      s0 = tfma(VmD + D, D, s0);
-      s1 = tfma(D, D, s1);
-      s2 = tfma(VmD, VmD, s2);
-    }
-    red[0].add(s0);
-    red[1].add(s1);
-    red[2].add(s2);
-  }
-};
-
 template <class T>
 struct OpScale : OpBase {
   T* u; T s;
@@ -193,21 +67,6 @@ struct OpNorm2 : OpBase {
     T s = (T)0;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) s = tfma(a[k], a[k], s);
-    red[0].add(s);
-  }
-};
-
-template <class T>
-struct OpDot : OpBase {
-  const T* a; const T* b;
-  __device__ void operator()(int64_t v, Acc<T>* red) const {
-    constexpr int VEC = V16<T>::N;
-    T x[VEC], y[VEC];
-    HL_LOAD(a, v, x);
-    HL_LOAD(b, v, y);
-    T s = (T)0;
-#pragma unroll
-    for (int k = 0; k < VEC; ++k) s = tfma(x[k], y[k], s);
     red[0].add(s);
   }
 };
@@ -362,49 +221,6 @@ __global__ void k_trace_fix(T* dst, const T* src, const double* dscal, double ad
 
 }  // namespace
 
-void launch_fista_xt(Ctx* c, void* xt, const void* y, const void* x, double A, double a, int ld) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  const double wy = A / (A + a), wx = a / (A + a);
-  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXt<T>{{}, (T*)xt, (const T*)y, (const T*)x, (T)wy, (T)wx},
-                                 -1));
-}
-
-void launch_fista_x_xt(Ctx* c, void* x, const void* y, void* xt, double mu, double a,
-                       double tk, double tk_new, double L, double A_next, double a_next, int ld) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  const double cy = (mu * a + a * (L - mu)) / tk_new;
-  const double cx = tk / tk_new;
-  const double cxt = -a * (L - mu) / tk_new;
-  const double wy = A_next / (A_next + a_next), wx = a_next / (A_next + a_next);
-  HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpXXt<T>{{}, (T*)x, (T*)xt, (const T*)y, (T)cy, (T)cx,
-                                                 (T)cxt, (T)wy, (T)wx}, -1));
-}
-
-void launch_fista_z(Ctx* c, void* z, const void* xt, const void* W, const void* center,
-                    double lam, double L, int ld) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  const double c2lam = 2.0 * lam, invL = 1.0 / L;
-  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpZ<T>{{}, (T*)z, (const T*)xt, (const T*)W,
-                                               (const T*)center, (T)c2lam, (T)invL}, S_SCALE));
-}
-
-void launch_fista_y(Ctx* c, void* y, const void* z, const void* xt, const void* center,
-                    const void* W, double lam, double tau, int ld) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  const double* z2 = c->d_scal + S_SCALE;
-  const double c2lam = 2.0 * lam;
-  HL_BY_TYPE(c, run_stream<T, 4>(c, ne, OpY<T>{(T*)y, (const T*)z, (const T*)xt, (const T*)center,
-                                               (const T*)W, z2, tau, (T)c2lam, (T)0}, S_VEC));
-}
-
-void launch_aipp_check(Ctx* c, const void* Wy, const void* z, const void* y, const void* center,
-                       double lam, double L, int ld) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  const double c2lam = 2.0 * lam;
-  HL_BY_TYPE(c, run_stream<T, 3>(c, ne, OpAipp<T>{{}, (const T*)Wy, (const T*)z, (const T*)y,
-                                                  (const T*)center, (T)c2lam, (T)L}, S_VEC2));
-}
-
 void launch_scale(Ctx* c, void* U, int ld, double s) {
   const int64_t ne = c->P.n * (int64_t)ld;
   HL_BY_TYPE(c, run_stream<T, 0>(c, ne, OpScale<T>{{}, (T*)U, (T)s}, -1));
@@ -413,11 +229,6 @@ void launch_scale(Ctx* c, void* U, int ld, double s) {
 void launch_norm2(Ctx* c, const void* U, int ld, int slot) {
   const int64_t ne = c->P.n * (int64_t)ld;
   HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpNorm2<T>{{}, (const T*)U}, slot));
-}
-
-void launch_dot(Ctx* c, const void* W, const void* U, int ld, int slot) {
-  const int64_t ne = c->P.n * (int64_t)ld;
-  HL_BY_TYPE(c, run_stream<T, 1>(c, ne, OpDot<T>{{}, (const T*)W, (const T*)U}, slot));
 }
 
 void launch_trace_fix(Ctx* c, void* r, const void* src, const double* dscal, double add) {

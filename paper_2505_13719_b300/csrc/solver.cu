@@ -1,9 +1,16 @@
 // HALLaR driver (Alg. 1) with ADAP-AIPP / ADAP-FISTA (Appendix A) on device
-// data.  The host holds only scalars: every vector (U, the FISTA sequences,
-// multipliers, residuals, Lanczos vectors) stays in HBM for the whole solve
-// (Section 3.1), and each FISTA iteration costs one device->host transfer of
-// the reduction slots.  The control flow and its readings of the paper's
-// open points are the same as the oracle's:
+// data.  Every vector (U, the ADAP-FISTA sequences, multipliers, residuals,
+// Lanczos vectors) stays in HBM for the whole solve (Section 3.1).  Each
+// ADAP-AIPP call runs on the device (loop.cu): its scalar recurrences live in
+// a LoopCtl in device memory, and the call is one CUDA graph of two nested
+// WHILE nodes (ADAP-FISTA calls, and each call's trials), replayed until the
+// call is done, so the host synchronises once per graph launch instead of
+// once per trial.  With kernel timing on (hallar_profile) the same kernels
+// run one launch at a time, the host reading the loop conditions.  The HLR
+// loop, Lanczos, Frank-Wolfe and the AL outer loop stay on the host.
+//
+// The control flow and its readings of the paper's open points are the same
+// as the oracle's:
 //   * epsilon_t = max(tol/2 (1 + |pval|), eps_1 eps_decay^(t-1)),
 //     eps_1 = eps1_rel (1 + tau^2 ||C||_1); ADAP-AIPP gets rho = epsilon_t / tau;
 //   * beta doubles (<= beta_max) when ||r_t|| > ||r_{t-1}|| / 4 while the
@@ -25,6 +32,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "device_common.cuh"
@@ -80,6 +88,26 @@ struct GradScal {
   double T0 = 0, pr = 0, rr = 0, nrm2 = 0, g = 0, mag = 0;
 };
 
+// ADAP-FISTA calls per graph launch of an ADAP-AIPP call: the host checks
+// the time limit between launches
+constexpr int kAttemptsPerLaunch = 64;
+
+// a CUDA graph of one ADAP-AIPP call for a factor width
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int ld = -1;
+  unsigned long long h_fista = 0, h_aipp = 0;
+  int64_t k_top = 0, k_outer = 0, k_trial = 0;  // kernels per launch / call / trial
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    ld = -1;
+  }
+};
+
 struct Solver {
   Ctx* c;
   Problem& P;
@@ -87,27 +115,40 @@ struct Solver {
   int64_t n = 0, m = 0;
   int ld_max = 0;
   size_t fbytes = 0;  // bytes of one factor buffer
-  void *Ytil = nullptr, *ctr = nullptr, *x = nullptr, *y = nullptr, *xt = nullptr, *z = nullptr;
-  void *ynew = nullptr, *Wg = nullptr, *Wy = nullptr, *tmp = nullptr;
+  // factor buffers: pool[3] rotate as the prox centre / y / trial y (the HLR
+  // factor Y is pool[ic]); x, x~ and z of ADAP-FISTA
+  void* pool[3] = {nullptr, nullptr, nullptr};
+  void *xb = nullptr, *xtb = nullptr, *zb = nullptr;
+  int ic = 0;  // pool index of the HLR factor
   // p: the multipliers (double, the dual update's precision); pk: the copy of
   // the factor type that the operator kernels read (p itself in FP64);
-  // residual vectors have the factor type
+  // residual vectors have the factor type: rpool[ir] holds A(YY^T) - b at Y
   double *p = nullptr, *pshift = nullptr;
-  void *pk = nullptr, *r_ctr = nullptr, *rX = nullptr, *rY = nullptr;
+  void* pk = nullptr;
+  void* rpool[2] = {nullptr, nullptr};
+  void* rX = nullptr;
+  int ir = 0;
   double *v = nullptr, *vprev = nullptr, *v0 = nullptr;
+  LoopCtl* d_ctl = nullptr;  // device
+  LoopCtl* h_ctl = nullptr;  // pinned host mirror
+  LoopGraph graph;
   int rank = 0, ld = 0;
   double beta = 1.0, lam = 1.0, Mbar = 1.0, p_tr = 0.0, b_tr = 0.0;
   hallar_result R{};
   std::chrono::steady_clock::time_point t0;
 
   explicit Solver(Ctx* cc) : c(cc), P(cc->P), o(cc->opt) {}
+  ~Solver() { graph.release(); }
 
+  void* Y() const { return pool[ic]; }
+  void* rY() const { return rpool[ir]; }
   double tau() const { return std::sqrt(P.tau2); }
   // unit roundoff of the stored factor: rounding the iterates moves g by up
   // to about u * mag; the acceptance tests of ADAP-FISTA step 2 and
   // ADAP-AIPP step 2 allow kRoundSlack times that
   double unit() const { return o.precision == HALLAR_MIXED ? 0x1p-24 : 0x1p-53; }
   static constexpr double kRoundSlack = 16.0;
+  bool needs_colsum() const { return P.C_J != 0.0 || P.has_trace; }
   // the solver's own buffers (kept after the solve for hallar_get_solution)
   std::vector<void*> mine;
   template <class T>
@@ -123,17 +164,20 @@ struct Solver {
     m = P.m;
     ld_max = padded_ld(c, o.r_cap + 1);
     fbytes = (size_t)n * ld_max * elem_size(c);
-    Ytil = fbuf(); ctr = fbuf(); x = fbuf(); y = fbuf(); xt = fbuf(); z = fbuf();
-    ynew = fbuf(); Wg = fbuf(); Wy = fbuf(); tmp = fbuf();
+    for (auto& b : pool) b = fbuf();
+    xb = fbuf();
+    xtb = fbuf();
+    zb = fbuf();
     p = salloc<double>(m);
     pk = o.precision == HALLAR_MIXED ? (void*)salloc<float>(m) : (void*)p;
-    r_ctr = salloc<unsigned char>(m * elem_size(c));
+    for (auto& b : rpool) b = salloc<unsigned char>(m * elem_size(c));
     rX = salloc<unsigned char>(m * elem_size(c));
-    rY = salloc<unsigned char>(m * elem_size(c));
     pshift = salloc<double>(m);
     v = salloc<double>(n);
     vprev = salloc<double>(n);
     v0 = salloc<double>(n);
+    d_ctl = salloc<LoopCtl>(1);
+    h_ctl = reinterpret_cast<LoopCtl*>(c->h_scal + S_COUNT);
     if (P.has_trace) {
       HL_CUDA(cudaMemcpyAsync(&b_tr, P.b + (m - 1), sizeof(double), cudaMemcpyDeviceToHost,
                               c->stream));
@@ -141,15 +185,6 @@ struct Solver {
     }
   }
 
-  void copyf(void* dst, const void* src) {
-    HL_CUDA(cudaMemcpyAsync(dst, src, (size_t)n * ld * elem_size(c), cudaMemcpyDeviceToDevice,
-                            c->stream));
-  }
-
-  // trace-row entry of a residual vector from a device scalar
-  void trace_fix(void* r, const void* src, const double* dscal, double add) {
-    launch_trace_fix(c, r, src, dscal, add);
-  }
   // the kernels' copy of p after p changed
   void refresh_pk() {
     if (pk != (void*)p) launch_to_factor_type(c, m, pk, p);
@@ -157,9 +192,9 @@ struct Solver {
 
   // enqueue: pre-pass + fused operator at U (W and resid optional)
   void grad_enqueue(const void* U, void* W, void* resid) {
-    if (P.C_J != 0.0 || P.has_trace) launch_colsum(c, U, ld, c->d_colsum, S_PRE);
+    if (needs_colsum()) launch_colsum(c, U, ld, c->d_colsum, S_PRE);
     launch_grad(c, U, ld, rank, pk, beta, GradOut{W, resid, nullptr});
-    if (resid && P.has_trace) trace_fix(resid, nullptr, c->d_scal + S_PRE, -b_tr);
+    if (resid && P.has_trace) launch_trace_fix(c, resid, nullptr, c->d_scal + S_PRE, -b_tr);
     R.grad_evals++;
   }
   GradScal grad_read() const {
@@ -179,26 +214,6 @@ struct Solver {
     s.g = s.T0 + s.pr + 0.5 * beta * s.rr;
     return s;
   }
-  // enqueue: g(Y) - g(X) pieces (rY = A(YY^T) - b when rY != null)
-  void change_enqueue(const void* X, const void* Yv, const void* rXv, void* rYv) {
-    if (P.C_J != 0.0)
-      launch_colsum_diff(c, X, Yv, ld, c->d_colsum + kColsumMax, c->d_colsum + 2 * kColsumMax);
-    launch_value_change(c, X, Yv, ld, rank, pk, rXv, rYv);
-    if (rYv && P.has_trace) trace_fix(rYv, rXv, c->d_scal + S_DIFF + 3, 0.0);
-    R.value_evals++;
-  }
-  double change_read(double nrmX2) const {
-    const double* h = c->h_scal;
-    const double dT0 = h[S_DIFF] + (P.C_J != 0.0 ? P.C_J * h[S_DIFF + 5] : 0.0);
-    double pd = h[S_DIFF + 1], q = h[S_DIFF + 2];
-    if (P.has_trace) {
-      const double dt = h[S_DIFF + 3];
-      const double rx = nrmX2 - b_tr;
-      pd += p_tr * dt;
-      q += dt * (2.0 * rx + dt);
-    }
-    return dT0 + pd + 0.5 * beta * q;
-  }
   void fetch() { fetch_scalars(c, 0, S_COUNT); }
 
   void check_time() {
@@ -206,135 +221,215 @@ struct Solver {
     if (el > o.time_limit_s) throw Err{HALLAR_ETIMEOUT, "time limit reached"};
   }
 
-  // step 2's a_j for the trial stepsize Ln (the positive root of
-  // (Ln - mu) a^2 = tk (A + a))
-  static double next_a(double tk, double A, double Ln, double mu) {
-    return (tk + std::sqrt(tk * tk + 4.0 * tk * A * (Ln - mu))) / (2.0 * (Ln - mu));
+  // ---- the device-side ADAP-AIPP loop -------------------------------------
+  // one ADAP-FISTA trial: operator at x~ with the z epilogue, the value
+  // change to y = P_B(z) with the prox sums, control, x / x~ updates
+  void enqueue_trial() {
+    if (needs_colsum()) launch_colsum_ind(c, ld, &d_ctl->c_trial);
+    launch_grad_epi(c, EPI_FISTA_Z, ld, rank, pk, &d_ctl->g_trial);
+    if (P.C_J != 0.0) launch_colsum_diff_ind(c, ld, &d_ctl->cd_trial);
+    launch_value_change_ind(c, true, ld, rank, pk, &d_ctl->v_trial);
+    launch_fista_ctl(c, d_ctl);
+    launch_loop_x(c, ld, d_ctl);
+  }
+  // after an ADAP-FISTA call: ADAP-AIPP step 2 at its output y
+  void enqueue_check() {
+    if (needs_colsum()) launch_colsum_ind(c, ld, &d_ctl->c_check);
+    launch_grad_epi(c, EPI_AIPP, ld, rank, pk, &d_ctl->g_check);
+    if (P.has_trace) launch_trace_fix_ind(c, &d_ctl->t_check, -b_tr);
+    if (P.C_J != 0.0) launch_colsum_diff_ind(c, ld, &d_ctl->cd_check);
+    launch_value_change_ind(c, false, ld, rank, pk, &d_ctl->v_check);
+    launch_aipp_ctl(c, d_ctl);
   }
 
-  // ADAP-FISTA on psi_s = lam g + 1/2 |. - ctr|^2 from x0 = ctr.
-  // On success ynew holds y, z its unprojected step and *Lout the final L.
-  bool fista(double lamv, double mu, double L0, double* Lout) {
-    copyf(x, ctr);
-    copyf(y, ctr);
-    double A = 0.0, tk = 1.0, L = L0;
-    const double tauv = tau();
-    bool xt_ready = false;  // x~ of the first trial already formed by step 3's pass
-    for (int it = 0; it < o.max_fista; ++it) {
-      R.fista_iters++;
-      if ((it & 15) == 15) check_time();
-      double Ln = L, a = 0.0, d2 = 0.0, dy0 = 0.0;
-      for (;;) {                                                 // step 2
-        a = next_a(tk, A, Ln, mu);
-        if (xt_ready) xt_ready = false;
-        else if (A == 0.0) copyf(xt, x);
-        else launch_fista_xt(c, xt, y, x, A, a, ld);
-        grad_enqueue(xt, Wg, rX);
-        launch_fista_z(c, z, xt, Wg, ctr, lamv, Ln, ld);
-        launch_fista_y(c, ynew, z, xt, ctr, Wg, lamv, tauv, ld);
-        change_enqueue(xt, ynew, rX, rY);
-        fetch();
-        const double nrm_xt2 = c->h_scal[S_PRE];
-        d2 = c->h_scal[S_VEC];
-        const double gd = c->h_scal[S_VEC + 1];
-        const double dlin = c->h_scal[S_VEC + 2];
-        dy0 = c->h_scal[S_VEC + 3];
-        const double dpsi = lamv * change_read(nrm_xt2) + dlin;
-        const double slack = kRoundSlack * unit() * lamv * grad_read().mag;
-        if (!std::isfinite(dpsi) || !std::isfinite(gd))
-          throw Err{HALLAR_ENUMERIC, "non-finite ADAP-FISTA step"};
-        if (o.verbose >= 3)
-          std::fprintf(stderr, "[fista] it=%d L=%.3e d2=%.3e gd=%.6e dpsi=%.6e dy0=%.3e\n", it, Ln,
-                       d2, gd, dpsi, dy0);
-        if (gd + (1.0 - o.chi) * Ln / 4.0 * d2 >= dpsi - slack) break;
-        Ln *= 2.0;
-        if (Ln > 1e30) {
-          R.fista_failures++;
-          *Lout = Ln;
-          return false;
+  // Capture the ADAP-AIPP call as a graph: [reset] -> WHILE(aipp) {
+  // begin -> WHILE(fista) { trial } -> check }.  Nothing allocates while
+  // capturing (every buffer exists), and kernel timing is off.
+  void build_graph() {
+    graph.release();
+    cudaStream_t s = c->stream;
+    const int64_t launches0 = c->launches;
+    c->capturing = true;
+    struct CaptureGuard {
+      Ctx* c;
+      ~CaptureGuard() {
+        c->capturing = false;
+        cudaStreamCaptureStatus st;
+        if (cudaStreamIsCapturing(c->stream, &st) == cudaSuccess &&
+            st != cudaStreamCaptureStatusNone) {
+          cudaGraph_t junk = nullptr;
+          cudaStreamEndCapture(c->stream, &junk);
+          if (junk) cudaGraphDestroy(junk);
         }
+        cudaGetLastError();
       }
-      const double A_new = A + a, tk_new = tk + a * mu;            // step 3
-      const double snorm = (Ln - mu) * std::sqrt(d2);
-      *Lout = Ln;
-      // steps 4 and 5 read only scalars of this trial, and x_{j+1} serves
-      // only later iterations: an iteration that returns skips its update
-      if (dy0 < o.chi * A_new * Ln * d2) {                          // step 4
-        R.fista_failures++;
-        return false;
-      }
-      if (snorm <= o.sigma * std::sqrt(dy0)) return true;           // step 5
-      // step 3's x update; the next iteration's first trial keeps L = Ln,
-      // so its x~ comes out of the same pass
-      launch_fista_x_xt(c, x, ynew, xt, mu, a, tk, tk_new, Ln, A_new,
-                        next_a(tk_new, A_new, Ln, mu), ld);
-      xt_ready = true;
-      std::swap(y, ynew);
-      A = A_new;
-      tk = tk_new;
-      L = Ln;
-    }
-    R.fista_failures++;
-    return false;
+    } guard{c};
+    HL_CUDA(cudaGraphCreate(&graph.graph, 0));
+    cudaGraphConditionalHandle ha, hf;
+    HL_CUDA(cudaGraphConditionalHandleCreate(&ha, graph.graph, 1, cudaGraphCondAssignDefault));
+    // top level: reset, then the ADAP-AIPP WHILE node
+    HL_CUDA(cudaStreamBeginCaptureToGraph(s, graph.graph, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    launch_loop_reset(c, d_ctl);
+    cudaGraph_t body_a = add_while(s, ha);
+    HL_CUDA(cudaStreamEndCapture(s, &graph.graph));
+    graph.k_top = c->launches - launches0;
+    // ADAP-AIPP body: begin, the ADAP-FISTA WHILE node, the step-2 check
+    HL_CUDA(cudaGraphConditionalHandleCreate(&hf, body_a, 0, 0));
+    int64_t l1 = c->launches;
+    HL_CUDA(cudaStreamBeginCaptureToGraph(s, body_a, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    launch_aipp_begin(c, d_ctl);
+    cudaGraph_t body_f = add_while(s, hf);
+    enqueue_check();
+    cudaGraph_t tmp = body_a;
+    HL_CUDA(cudaStreamEndCapture(s, &tmp));
+    graph.k_outer = c->launches - l1;
+    // ADAP-FISTA body: one trial
+    l1 = c->launches;
+    HL_CUDA(cudaStreamBeginCaptureToGraph(s, body_f, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    enqueue_trial();
+    tmp = body_f;
+    HL_CUDA(cudaStreamEndCapture(s, &tmp));
+    graph.k_trial = c->launches - l1;
+    c->launches = launches0;  // captured, not launched
+    HL_CUDA(cudaGraphInstantiate(&graph.exec, graph.graph, 0));
+    graph.ld = ld;
+    graph.h_fista = (unsigned long long)hf;
+    graph.h_aipp = (unsigned long long)ha;
   }
 
-  // ADAP-AIPP from Ytil; on return Ytil holds W, Wy = (C + A*(p'))W, rY its
-  // residual and *gs the operator scalars at W.
-  void aipp(double rho, GradScal* gs) {
-    copyf(ctr, Ytil);
-    grad_enqueue(ctr, nullptr, r_ctr);
+  // add a WHILE node after the capture's current dependencies; the capture
+  // continues after it.  Returns the node's body graph.
+  cudaGraph_t add_while(cudaStream_t s, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    HL_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    if (st != cudaStreamCaptureStatusActive) fail(HALLAR_ECUDA, "graph capture is not active");
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    HL_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+    HL_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies));
+    return np.conditional.phGraph_out[0];
+  }
+
+  // ADAP-AIPP (Appendix A) from Y = pool[ic]; on return pool[ic] holds W,
+  // rpool[ir] its residuals, *gs the operator scalars at W and *GdotX
+  // G . WW^T = <(C + A*(p'))W, W>.
+  void aipp(double rho, GradScal* gs, double* GdotX) {
+    // residuals at the centre and |centre|^2 (trace row)
+    grad_enqueue(Y(), nullptr, rpool[ir]);
     fetch();
-    double nrm_ctr2 = c->h_scal[S_PRE];
-    for (int j = 0; j < o.max_aipp; ++j) {
-      R.aipp_iters++;
-      check_time();
-      double L = 1.0, VmD2 = 0.0;
-      bool stalled = false;
-      GradScal gy;
-      for (;;) {
-        const double Mlow = std::fmax(1.0, Mbar / 2.0);            // step 1
-        if (fista(lam, 0.5, Mlow, &L)) {
-          grad_enqueue(ynew, Wy, rY);
-          change_enqueue(ctr, ynew, r_ctr, nullptr);
-          launch_aipp_check(c, Wy, z, ynew, ctr, lam, L, ld);
-          fetch();
-          gy = grad_read();
-          const double dg = change_read(nrm_ctr2);
-          const double VD = c->h_scal[S_VEC2];
-          const double D2 = c->h_scal[S_VEC2 + 1];
-          VmD2 = c->h_scal[S_VEC2 + 2];
-          if (o.verbose >= 2)
-            std::fprintf(stderr, "[aipp] j=%d lam=%.3e L=%.3e dg=%.6e D2=%.3e VD=%.6e |R|=%.3e rho=%.3e\n",
-                         j, lam, L, dg, D2, VD, std::sqrt(VmD2) / lam, rho);
-          const double slack = kRoundSlack * unit() * lam * gy.mag;
-          stalled = D2 == 0.0;
-          if (stalled || -lam * dg - 0.5 * D2 >= -VD - slack) break;  // step 2
-        }
-        lam /= 2.0;
-        if (lam < 1e-30) throw Err{HALLAR_ENUMERIC, "ADAP-AIPP: prox stepsize underflow"};
-      }
-      Mbar = L;
-      const double Rn = std::sqrt(VmD2) / lam;                      // |R_j|, eq. Rj def
-      std::swap(ctr, ynew);  // the accepted point is the next prox centre
-      std::swap(r_ctr, rY);
-      nrm_ctr2 = gy.nrm2;
-      // step 3; a prox step that left W unchanged (below the resolution of
-      // the stored factor) cannot make further progress: stop there too
-      if (Rn <= rho || stalled || j + 1 == o.max_aipp) {
-        std::swap(Ytil, ctr);
-        std::swap(rY, r_ctr);
-        *gs = gy;
-        return;
-      }
+    const double nrm_ctr2 = c->h_scal[S_PRE];
+    const bool eager = c->prof_on;  // per-kernel timing needs launches of their own
+    LoopCtl& H = *h_ctl;
+    std::memset(&H, 0, sizeof(LoopCtl));
+    for (int k = 0; k < 3; ++k) H.pool[k] = pool[k];
+    H.xb = xb;
+    H.xtb = xtb;
+    H.zb = zb;
+    H.rpool[0] = rpool[0];
+    H.rpool[1] = rpool[1];
+    H.rX = rX;
+    H.i_ctr = ic;
+    H.i_rctr = ir;
+    H.mixed = o.precision == HALLAR_MIXED;
+    H.has_trace = P.has_trace;
+    H.beta = beta;
+    H.tau = tau();
+    H.chi = o.chi;
+    H.sigma = o.sigma;
+    H.mu = 0.5;
+    H.slack_u = kRoundSlack * unit();
+    H.rho = rho;
+    H.C_J = P.C_J;
+    H.b_tr = b_tr;
+    H.p_tr = p_tr;
+    H.max_fista = o.max_fista;
+    H.max_aipp = o.max_aipp;
+    H.attempt_cap = eager ? (1 << 30) : kAttemptsPerLaunch;
+    H.trial_cap = o.max_fista * 128;
+    H.lam = lam;
+    H.Mbar = Mbar;
+    H.nrm_ctr2 = nrm_ctr2;
+    H.graph_mode = eager ? 0 : 1;
+    if (!eager) {
+      if (graph.ld != ld) build_graph();
+      H.h_fista = graph.h_fista;
+      H.h_aipp = graph.h_aipp;
     }
+    HL_CUDA(cudaMemcpyAsync(d_ctl, &H, sizeof(LoopCtl), cudaMemcpyHostToDevice, c->stream));
+    if (eager) {
+      int32_t* flag = reinterpret_cast<int32_t*>(c->h_scal + S_SCALE + 6);
+      for (;;) {
+        launch_aipp_begin(c, d_ctl);
+        do {
+          enqueue_trial();
+          HL_CUDA(cudaMemcpyAsync(flag, &d_ctl->cont_fista, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, c->stream));
+          sync(c);
+        } while (*flag);
+        enqueue_check();
+        HL_CUDA(cudaMemcpyAsync(flag, &d_ctl->cont_aipp, sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        if (!*flag) break;
+        check_time();
+      }
+      HL_CUDA(cudaMemcpyAsync(&H, d_ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->stream));
+      sync(c);
+    } else {
+      for (;;) {
+        HL_CUDA(cudaGraphLaunch(graph.exec, c->stream));
+        HL_CUDA(cudaMemcpyAsync(&H, d_ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, c->stream));
+        sync(c);
+        c->launches += graph.k_top;
+        if (H.done || H.error) break;
+        check_time();
+      }
+      c->launches += graph.k_outer * H.n_attempts + graph.k_trial * H.n_trials;
+    }
+    R.fista_iters += (int32_t)H.n_fista_iters;
+    R.fista_failures += (int32_t)H.n_fista_fail;
+    R.aipp_iters += (int32_t)H.n_aipp_iters;
+    R.grad_evals += H.n_grads;
+    R.value_evals += H.n_values;
+    if (H.error == HALLAR_ENUMERIC)
+      throw Err{HALLAR_ENUMERIC, "non-finite ADAP-FISTA step or prox stepsize underflow"};
+    if (H.error) throw Err{(hallar_status)H.error, "ADAP-FISTA trial limit reached"};
+    lam = H.lam;
+    Mbar = H.Mbar;
+    ic = H.i_ctr;
+    ir = H.i_rctr;
+    gs->T0 = H.gT0;
+    gs->pr = H.gpr;
+    gs->rr = H.grr;
+    gs->nrm2 = H.gnrm2;
+    gs->mag = H.gmag;
+    gs->g = H.gT0 + H.gpr + 0.5 * beta * H.grr;
+    *GdotX = H.gWU;
+    if (o.verbose >= 2)
+      std::fprintf(stderr, "[aipp] lam=%.3e Mbar=%.3e |R|=%.3e rho=%.3e fista=%lld trials=%lld\n",
+                   lam, Mbar, H.Rn, rho, H.n_fista_iters, H.n_trials);
   }
+
+  // the pool index other than ic and `busy` (the destination of a new factor)
+  int free_slot() const { return (ic + 1) % 3; }
 
   void trim_rank() {
-    // keep the r_cap leading eigenvectors of Y^T Y (Y = Ytil, rank columns)
+    // keep the r_cap leading eigenvectors of Y^T Y (Y = pool[ic], rank columns)
     const int k = o.r_cap;
     const int ld_new = padded_ld(c, k);
-    trim_factor(c, Ytil, ld, rank, k, tmp, ld_new, nullptr);
-    std::swap(Ytil, tmp);
+    const int dst = free_slot();
+    trim_factor(c, Y(), ld, rank, k, pool[dst], ld_new, nullptr);
+    ic = dst;
     rank = k;
     ld = ld_new;
     R.trims++;
@@ -346,14 +441,16 @@ struct Solver {
     // initial factor: padded copy, projected onto the ball
     rank = r0;
     ld = padded_ld(c, r0);
-    launch_pad_copy(c, U0d, r0, Ytil, ld, r0, 1.0);
-    launch_norm2(c, Ytil, ld, S_VEC);
+    ic = 0;
+    ir = 0;
+    launch_pad_copy(c, U0d, r0, Y(), ld, r0, 1.0);
+    launch_norm2(c, Y(), ld, S_VEC);
     if (p0d) HL_CUDA(cudaMemcpyAsync(p, p0d, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     else HL_CUDA(cudaMemsetAsync(p, 0, m * sizeof(double), c->stream));
     refresh_pk();
     fetch();
     const double nU = std::sqrt(c->h_scal[S_VEC]);
-    if (nU > tauv) launch_scale(c, Ytil, ld, tauv / nU);
+    if (nU > tauv) launch_scale(c, Y(), ld, tauv / nU);
     if (P.has_trace) {
       HL_CUDA(cudaMemcpyAsync(&c->h_scal[S_SCALE + 3], p + (m - 1), sizeof(double),
                               cudaMemcpyDeviceToHost, c->stream));
@@ -366,7 +463,7 @@ struct Solver {
     const double eps1 = o.eps1_rel * (1.0 + P.tau2 * P.c_norm1);
     double prev_rnorm = INFINITY;
     bool have_vprev = false;
-    grad_enqueue(Ytil, nullptr, nullptr);  // pval at the start point
+    grad_enqueue(Y(), nullptr, nullptr);  // pval at the start point
     fetch();
     double pval_now = grad_read().T0;
     double theta = 0.0, lam_min = 0.0;
@@ -379,13 +476,11 @@ struct Solver {
       const double rho_t = eps_t / std::fmax(tauv, 1e-300);
       for (int hl = 0; hl < o.max_hlr; ++hl) {                      // HLR
         R.hlr_iters++;
-        aipp(rho_t, &gs);                                           // step 6
-        launch_dot(c, Wy, Ytil, ld, S_VEC);                         // G . YY^T = <GY, Y>
-        launch_axpy_t(c, m, pshift, p, rY, beta);                   // p' = p + beta r(Y)
+        double GdotX = 0.0;                                         // G . YY^T = <GY, Y>
+        aipp(rho_t, &gs, &GdotX);                                   // step 6
+        launch_axpy_t(c, m, pshift, p, rY(), beta);                 // p' = p + beta r(Y)
         const uint64_t sd = o.seed + 7919ull * (uint64_t)R.hlr_iters;
         launch_splitmix(c, sd, v0, 0.1 / std::sqrt((double)n), have_vprev ? vprev : nullptr);
-        fetch();
-        const double GdotX = c->h_scal[S_VEC];
         const double eig_tol = o.lanczos_tol_rel * eps_t / P.tau2;  // step 7
         const LanczosOut le = lanczos_min_eig(c, pshift, v0, eig_tol, o.lanczos_kmax, 50, v);
         R.lanczos_iters += le.iters;
@@ -397,7 +492,7 @@ struct Solver {
         if (gap <= eps_t) break;                                    // step 8
         if (hl + 1 == o.max_hlr) break;                             // HLR limit: keep Y
         // Frank-Wolfe step (eqs. FW stepsize, tilde Y)              // step 11
-        launch_fw_denom(c, v, rY, theta > 0.0 ? P.tau2 : 0.0, S_VEC2);
+        launch_fw_denom(c, v, rY(), theta > 0.0 ? P.tau2 : 0.0, S_VEC2);
         fetch();
         double ssq = c->h_scal[S_VEC2];
         if (P.has_trace) {
@@ -408,31 +503,32 @@ struct Solver {
         const double alpha = denom <= 0.0 ? 1.0 : std::fmin(gap / denom, 1.0);
         R.fw_steps++;
         int ldn = ld;
+        const int dst = free_slot();
         if (theta > 0.0) {
           if (alpha >= 1.0) {
             ldn = padded_ld(c, 1);
-            launch_fw_append(c, Ytil, ld, 0, v, 0.0, tauv, tmp, ldn, 1);
+            launch_fw_append(c, Y(), ld, 0, v, 0.0, tauv, pool[dst], ldn, 1);
             rank = 1;
           } else {
             ldn = padded_ld(c, rank + 1);
-            launch_fw_append(c, Ytil, ld, rank, v, std::sqrt(1.0 - alpha),
-                             std::sqrt(alpha) * tauv, tmp, ldn, 1);
+            launch_fw_append(c, Y(), ld, rank, v, std::sqrt(1.0 - alpha),
+                             std::sqrt(alpha) * tauv, pool[dst], ldn, 1);
             rank += 1;
           }
         } else if (alpha >= 1.0) {
           ldn = padded_ld(c, 1);
-          launch_fw_append(c, Ytil, ld, 0, v, 0.0, 0.0, tmp, ldn, 0);
+          launch_fw_append(c, Y(), ld, 0, v, 0.0, 0.0, pool[dst], ldn, 0);
           rank = 1;
         } else {
-          launch_fw_append(c, Ytil, ld, rank, v, std::sqrt(1.0 - alpha), 0.0, tmp, ld, 0);
+          launch_fw_append(c, Y(), ld, rank, v, std::sqrt(1.0 - alpha), 0.0, pool[dst], ld, 0);
         }
         ld = ldn;
-        std::swap(Ytil, tmp);
+        ic = dst;
         if (rank > o.r_cap) trim_rank();
         check_time();
       }
       // U_t = Y; dual update p_t = p + beta r (step 14)
-      launch_axpy_t(c, m, p, p, rY, beta);
+      launch_axpy_t(c, m, p, p, rY(), beta);
       refresh_pk();
       if (P.has_trace) p_tr += beta * (gs.nrm2 - b_tr);
       launch_dvec(c, 1, m, nullptr, P.b, p, 0.0, S_VEC2 + 4);
@@ -475,7 +571,7 @@ struct Solver {
     }
     sync(c);
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    c->sol_U = Ytil;
+    c->sol_U = Y();
     c->sol_rank = rank;
     c->sol_ld = ld;
     c->sol_p = p;
@@ -538,8 +634,8 @@ hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_res
       *res = s.R;
       res->kernel_launches = c->launches - launches0;
     }
-    if (e.st == HALLAR_ETIMEOUT && s.Ytil) {
-      c->sol_U = s.Ytil;
+    if (e.st == HALLAR_ETIMEOUT && s.pool[s.ic]) {
+      c->sol_U = s.Y();
       c->sol_rank = s.rank;
       c->sol_ld = s.ld;
       c->sol_p = s.p;

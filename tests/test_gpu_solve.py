@@ -173,3 +173,29 @@ def test_repeated_solves_on_one_handle(H, prec):
         out = [H.hallar_solve(hd.h, U0, 2) for _ in range(3)]
     assert all(st == H.HALLAR_OK for st, _ in out)
     assert out[0][1].pval == out[1][1].pval == out[2][1].pval
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("make", [lambda: I.maxcut(64, *I.er_graph(64, 0.1, 3)),
+                                  lambda: I.theta(9, *I.cycle_graph(9)),
+                                  lambda: I.theta_gnm(40, 80, seed=3)],
+                         ids=["maxcut_er64", "theta_C9", "theta_gnm40"])
+def test_graph_loop_matches_kernel_by_kernel_loop(H, make, prec):
+    # ADAP-AIPP runs on the device: as a CUDA graph of nested WHILE nodes,
+    # or (with kernel timing on) one launch at a time with the host reading
+    # the loop conditions.  The kernels are the same, so the solves must be
+    # identical bit for bit, counters included.
+    inst = make()
+    dt = np.float32 if prec else np.float64
+    U0 = I.initial_factor(inst.n, 2, 4).astype(dt)
+    with H.create_from_instance(inst, prec, tol=TOLS[prec], time_limit_s=60.0,
+                                max_outer=6) as hd:
+        st_g, r_g = H.hallar_solve(hd.h, U0, 2)
+        H.hallar_profile(hd.h, 1)
+        st_e, r_e = H.hallar_solve(hd.h, U0, 2)
+        ms, nl, _ = H.hallar_profile(hd.h, 2)
+    assert st_g == st_e
+    assert nl[0] > 0 and nl[1] > 0  # the kernel-by-kernel run was timed
+    for f in ("pval", "dval", "kkt", "rank", "fista_iters", "aipp_iters", "grad_evals",
+              "value_evals", "lanczos_iters", "fw_steps"):
+        assert getattr(r_g, f) == getattr(r_e, f), f
