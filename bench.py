@@ -10,12 +10,14 @@ one (float factor and SpMM, double for everything else); one FP64 solve of
 the same workload is reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload torus_unit|torus_pm1|er1000] [--precision mixed|fp64]
+                    [--workload torus_unit|torus_pm1|er1000|theta_gnm] [--precision mixed|fp64]
+                    [--kernel grad|change] [--serve] [--batch]
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (one gradient, one value change and a 20-step Lanczos run at full
-size) and projects its time to 1e-5 KKT with the per-solve operation counts
-recorded from a GPU solve of this workload (profiles/solve_counts.json).
+--impl reference times the FP64 CPU oracle as it stands on the host cores:
+each step is the oracle's own full solve of the workload's bounded sample
+(for the default workload the 32x32 twin of the torus), nothing projected.
+The same sample, solved by this library, is reported beside the CPU
+baseline of the default arm.
 """
 from __future__ import annotations
 
@@ -38,29 +40,37 @@ from paper_2505_13719_b300 import instances as I  # noqa: E402
 METRIC = "time to 1e-5 KKT & solves/s p50/p99, mixed-precision vs FP64, 1 B300"
 PROFILE_EVERY = 64  # kernel timing samples every 64th launch of each class
 TOL = 1e-5
-COUNTS_FILE = os.path.join(ROOT, "profiles", "solve_counts.json")
 
 WORKLOADS = {
     # the 1000 x 1000 toroidal grid of the Max-Cut configuration with unit
     # weights: its SDP optimum is the bipartite cut, 2e6, and is reached at
     # low rank; the +-1 weighted twin needs a rank far above 32 (see design notes)
     "torus_unit": dict(make=lambda: I.maxcut_torus(1000, "unit"), r0=10, u0_seed=1002,
-                       r_cap=32, exact=2.0e6,
-                       desc="Max-Cut SDP, 1000x1000 torus (n=1e6, 2e6 edges), unit weights"),
+                       r_cap=32, exact=2.0e6, precision="mixed",
+                       desc="Max-Cut SDP, 1000x1000 torus (n=1e6, 2e6 edges), unit weights",
+                       sample=dict(make=lambda: I.maxcut_torus(32, "unit"), r0=10, u0_seed=1002,
+                                   r_cap=32, desc="the 32x32 unit-weight torus (n=1024), "
+                                   "same family, weights, r0, U0 seed and tolerance")),
     "torus_pm1": dict(make=lambda: I.maxcut_torus(1000, "pm1", seed=2), r0=10, u0_seed=1002,
-                      r_cap=32, exact=None,
-                      desc="Max-Cut SDP, 1000x1000 torus (n=1e6, 2e6 edges), weights +-1"),
-    "er1000": dict(make=lambda: I.maxcut_er_1000(seed=1), r0=10, u0_seed=1001, r_cap=64,
-                   exact=None, desc="Max-Cut SDP, Erdos-Renyi G(1000, 0.01), unit weights"),
+                      r_cap=32, exact=None, precision="mixed",
+                      desc="Max-Cut SDP, 1000x1000 torus (n=1e6, 2e6 edges), weights +-1",
+                      sample=None),
+    "er1000": dict(make=lambda: I.maxcut_er_1000(seed=1), r0=10, u0_seed=1001, r_cap=32,
+                   exact=None, precision="fp64",
+                   desc="Max-Cut SDP, Erdos-Renyi G(1000, 0.01), unit weights",
+                   sample=dict(make=lambda: I.maxcut_er_1000(seed=1), r0=10, u0_seed=1001,
+                               r_cap=32, desc="the workload itself (full oracle solve)")),
     # the Lovasz theta configuration: G(n, M) with n = 1e5, M = 1e6 distinct
     # uniform edges, C = -11^T implicit, tr X = 1 row, tau^2 = 1
     "theta_gnm": dict(make=lambda: I.theta_gnm(100_000, 1_000_000, seed=3), r0=8,
-                      u0_seed=1003, r_cap=64, exact=None,
-                      desc="Lovasz theta SDP, G(n=1e5, M=1e6) random graph, trace row"),
+                      u0_seed=1003, r_cap=64, exact=None, precision="mixed",
+                      desc="Lovasz theta SDP, G(n=1e5, M=1e6) random graph, trace row",
+                      sample=None),
     # a small twin of torus_unit for profiler launch lists
     "torus_unit_64": dict(make=lambda: I.maxcut_torus(64, "unit"), r0=10, u0_seed=1002,
-                          r_cap=32, exact=2.0 * 64 * 64,
-                          desc="Max-Cut SDP, 64x64 torus (n=4096), unit weights"),
+                          r_cap=32, exact=2.0 * 64 * 64, precision="mixed",
+                          desc="Max-Cut SDP, 64x64 torus (n=4096), unit weights",
+                          sample=None),
 }
 
 
@@ -420,14 +430,16 @@ def run_ours(args, world, rank):
         st, res = H.hallar_solve(hd.h, U0, wl["r0"])
         return st, res
 
+    if args.eager:
+        # kernel by kernel (kernel timing on): what a profiler captures
+        H.hallar_profile(hd.h, 1)
+
     for _ in range(args.warmup):
         flush.zero_()
         one_solve()
-    # kernel timing live over the timed region, on the solve's stream: a CUDA
-    # event pair around every PROFILE_EVERY-th launch of each kernel class
-    # (sampling keeps the event overhead out of the headline)
-    H.hallar_profile_sampling(hd.h, PROFILE_EVERY)
-    H.hallar_profile(hd.h, 1)
+    # the timed solves run as they do for a user: each ADAP-AIPP call is one
+    # CUDA graph (kernel timing off); the kernel classes are timed in one
+    # more solve right after, launch by launch
     times, results = [], []
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier(world)
@@ -444,6 +456,16 @@ def run_ours(args, world, rank):
             results.append((st, res))
         barrier(world)
         wall = time.perf_counter() - t_all
+    # kernel classes: the same solve once more with per-launch CUDA events on
+    # the solve's stream (every PROFILE_EVERY-th launch of each class); the
+    # kernels are the graph's, launched one at a time
+    H.hallar_profile_sampling(hd.h, PROFILE_EVERY)
+    H.hallar_profile(hd.h, 1)
+    flush.zero_()
+    t0p = time.perf_counter()
+    one_solve()
+    torch.cuda.synchronize()
+    prof_solve_s = time.perf_counter() - t0p
     prof_ms, prof_n, prof_bytes, prof_pad = H.hallar_profile(hd.h, 2, padded=True)
     wall = all_max(world, wall)
     mean_t = all_max(world, statistics.mean(times))
@@ -473,18 +495,25 @@ def run_ours(args, world, rank):
                     / wl["exact"]}
     hd.close()
 
-    # FP64 comparison solve (same workload, not in the timed value)
-    fp64 = None
-    if not args.no_compare and prec == H.HALLAR_MIXED:
-        with H.create_from_instance(inst, H.HALLAR_FP64, **opts) as h64:
-            U64 = torch.from_numpy(U0h.astype(np.float64)).cuda()
+    # the same workload in the other precision form (not in the timed value):
+    # FP64 beside a mixed headline, mixed beside an FP64 one
+    other = None
+    if not args.no_compare:
+        oprec = H.HALLAR_FP64 if prec == H.HALLAR_MIXED else H.HALLAR_MIXED
+        odt = np.float64 if oprec == H.HALLAR_FP64 else np.float32
+        with H.create_from_instance(inst, oprec, **opts) as ho:
+            Uo = torch.from_numpy(U0h.astype(odt)).cuda()
+            H.hallar_solve(ho.h, Uo, wl["r0"])  # warm-up (graph instantiation, caches)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st64, r64 = H.hallar_solve(h64.h, U64, wl["r0"])
+            sto, ro = H.hallar_solve(ho.h, Uo, wl["r0"])
             torch.cuda.synchronize()
-            fp64 = {"time_s": round(time.perf_counter() - t0, 4), "status": int(st64),
-                    "kkt": r64.kkt, "pval": r64.pval,
-                    "rel_diff_pval_vs_mixed": abs(r64.pval - pval) / abs(r64.pval)}
+            to = time.perf_counter() - t0
+            other = {"precision": "fp64" if oprec == H.HALLAR_FP64 else "mixed",
+                     "time_s": round(to, 4), "status": int(sto),
+                     "kkt": ro.kkt, "pval": ro.pval, "grad_evals": int(ro.grad_evals),
+                     "rel_diff_pval": abs(ro.pval - pval) / abs(ro.pval),
+                     "headline_speedup": round(to / mean_t, 3)}
 
     # end to end through the public API with host buffers
     torch.cuda.synchronize()
@@ -519,7 +548,9 @@ def run_ours(args, world, rank):
                 "avg_launch_us": 1e3 * prof_ms[k] / max(1, prof_n[k]),
                 "timed_launches": int(prof_n[k]),
                 "sampling": f"every {PROFILE_EVERY}th launch of each class, CUDA events "
-                            "on the solve's stream, over the timed region",
+                            "on the solve's stream, in one solve after the timed region "
+                            f"(kernel by kernel: {prof_solve_s:.2f} s); the timed solves "
+                            "run the same kernels from CUDA graphs",
                 "classes": {names[j]: {"ms_sampled": round(prof_ms[j], 3),
                                        "timed_launches": int(prof_n[j]),
                                        "avg_launch_us": (1e3 * prof_ms[j] / prof_n[j]
@@ -530,9 +561,25 @@ def run_ours(args, world, rank):
                                                              / 1e9 if prof_ms[j] > 0 else None)}
                             for j in range(3)}}
 
+    # the CPU oracle on a bounded sample (rank 0), and this library on the
+    # same sample for a like-for-like ratio
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(inst, counts, args.cpu_budget)
+        cpu = cpu_baseline(wl, inst, int(round(counts["rank"])))
+        smp = wl.get("sample")
+        if smp is not None:
+            sinst = smp["make"]()
+            sU0 = I.initial_factor(sinst.n, smp["r0"], smp["u0_seed"]).astype(dt)
+            with H.create_from_instance(sinst, prec, tol=TOL, r_cap=smp["r_cap"],
+                                        time_limit_s=args.time_limit) as hs:
+                H.hallar_solve(hs.h, sU0, smp["r0"])  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sts, rs = H.hallar_solve(hs.h, sU0, smp["r0"])
+                torch.cuda.synchronize()
+                cpu["gpu_same_sample"] = {"time_s": round(time.perf_counter() - t0, 4),
+                                          "status": int(sts), "kkt": rs.kkt, "pval": rs.pval,
+                                          "precision": args.precision}
 
     line = {
         "metric": METRIC, "value": round(mean_t, 4), "unit": "s", "n_gpus": world,
@@ -550,7 +597,7 @@ def run_ours(args, world, rank):
         "tol_5e-6": tol2,
         "kkt": res_last.kkt, "pval": pval, "value_rel_err_vs_exact": value_check,
         "counts_per_solve": counts,
-        "fp64": fp64,
+        "other_precision": other,
         "e2e": {"value": round(e2e_t, 4), "unit": "s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "status": int(st2)},
         "gpu_launches": launches,
@@ -611,19 +658,38 @@ def load_peaks():
 # ---------------------------------------------------------------------------
 # the oracle on a bounded sample (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def cpu_baseline(inst, counts, budget_s):
-    """Time the FP64 oracle as it stands on one gradient, one value change and
-    a 20-step Lanczos run of the full-size workload, and project a solve with
-    the per-solve operation counts.  BLAS threads are pinned to one."""
-    try:
-        from threadpoolctl import threadpool_limits
-    except ImportError:  # pragma: no cover
-        threadpool_limits = None
+def oracle_threads():
+    """Threads the oracle may use: every host core for its BLAS calls (its
+    sparse products and row sums are single-threaded NumPy / SciPy)."""
+    return os.cpu_count() or 1
+
+
+def oracle_sample_solve(smp):
+    """The oracle's own full solve (its own trajectory, FP64) of the
+    workload's bounded sample to the bench tolerance; returns (seconds,
+    result)."""
+    from threadpoolctl import threadpool_limits
+
     from oracle import hallar_oracle as O
-    ctx = threadpool_limits(limits=1) if threadpool_limits else None
-    try:
+    sinst = smp["make"]()
+    U0 = I.initial_factor(sinst.n, smp["r0"], smp["u0_seed"])
+    with threadpool_limits(limits=oracle_threads()):
+        t0 = time.perf_counter()
+        res = O.hallar_solve(sinst, U0, opt=O.Options(tol=TOL, r_cap=smp["r_cap"]))
+        return time.perf_counter() - t0, res
+
+
+def cpu_baseline(wl, inst, rank):
+    """The FP64 oracle as it stands, on the host cores: its own full solve of
+    the workload's bounded sample (nothing projected, no count from the GPU
+    path), and its per-operator times at the workload's full size."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle import hallar_oracle as O
+    out = {"value": None, "unit": "s", "cores": oracle_threads(), "kind": "oracle"}
+    with threadpool_limits(limits=oracle_threads()):
         rng = np.random.default_rng(0)
-        r = max(2, int(round(counts.get("rank", 10))))
+        r = max(2, rank)
         U = rng.standard_normal((inst.n, r)) / math.sqrt(r)
         p = rng.standard_normal(inst.m) * 0.1
         t0 = time.perf_counter()
@@ -633,49 +699,55 @@ def cpu_baseline(inst, counts, budget_s):
         t0 = time.perf_counter()
         O.al_value_change(inst, U, Y, p, 1.0, gr.resid)
         t_change = time.perf_counter() - t0
-        kl = 20
+        kl = 10
         t0 = time.perf_counter()
         O.lanczos_min_eig(lambda x: O.gradient_matrix_apply(inst, gr.pshift, x), inst.n,
                           O.splitmix64_uniform(1, inst.n), tol=0.0, kmax=kl, max_restarts=0)
         t_lan = (time.perf_counter() - t0) / kl
-    finally:
-        if ctx is not None:
-            ctx.__exit__(None, None, None)
-    proj = (t_grad * counts["grad_evals"] + t_change * counts["value_evals"]
-            + t_lan * counts["lanczos_iters"])
-    return {"value": round(proj, 2), "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle timed on 1 gradient ({t_grad:.2f} s), 1 value change "
-                       f"({t_change:.2f} s) and 20 Lanczos steps ({t_lan:.3f} s/step) of the "
-                       f"full-size workload at rank {r}; projected with the per-solve counts "
-                       f"({int(counts['grad_evals'])} gradients, {int(counts['value_evals'])} "
-                       f"value changes, {int(counts['lanczos_iters'])} Lanczos steps); "
-                       f"streaming vector work is not counted, so this is a lower bound")}
+    out["per_op_full_size_s"] = {"gradient": round(t_grad, 4), "value_change": round(t_change, 4),
+                                 "lanczos_step": round(t_lan, 4), "rank": r}
+    smp = wl.get("sample")
+    if smp is None:
+        out["sample"] = ("per-operator times at full size only: no bounded full oracle solve "
+                         "exists for this workload")
+        return out
+    secs, res = oracle_sample_solve(smp)
+    out["value"] = round(secs, 3)
+    out["sample"] = (f"the oracle's own full FP64 solve of {smp['desc']} to {TOL:g} relative "
+                     f"KKT: {res.counters.grads} gradients, converged={bool(res.converged)}, "
+                     f"kkt {res.kkt:.2e}, pval {res.pval:.10g}; plus per-operator times at the "
+                     "workload's full size")
+    return out
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return None
     wl = WORKLOADS[args.workload]
-    if not os.path.exists(COUNTS_FILE):
-        return {"impl": "reference", "unavailable": "no recorded per-solve counts for the projection"}
-    counts = json.load(open(COUNTS_FILE)).get(args.workload)
-    if counts is None:
-        return {"impl": "reference", "unavailable": f"no recorded counts for {args.workload}"}
-    inst = wl["make"]()
-    vals = []
-    for _ in range(args.warmup + args.steps):
-        vals.append(cpu_baseline(inst, counts, args.cpu_budget))
-    timed = vals[args.warmup:]
-    v = statistics.mean(x["value"] for x in timed)
-    return {"impl": "reference", "metric": METRIC, "value": round(v, 2), "unit": "s",
+    smp = wl.get("sample")
+    if smp is None:
+        return {"impl": "reference",
+                "unavailable": "no bounded oracle sample is defined for this workload"}
+    vals, last = [], None
+    for k in range(args.warmup + args.steps):
+        secs, res = oracle_sample_solve(smp)
+        if k >= args.warmup:
+            vals.append(secs)
+            last = res
+    v = statistics.mean(vals)
+    sample = (f"each step: the oracle's own full FP64 solve of {smp['desc']} to {TOL:g} "
+              f"relative KKT ({last.counters.grads} gradients, kkt {last.kkt:.2e})")
+    inst_desc = wl["desc"]
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": wl["desc"], "precision": "fp64 (oracle)", "tol": TOL,
-                       "parallelism": "host cores"},
-            "cpu_baseline": {"value": round(v, 2), "unit": "s", "cores": 1, "kind": "oracle",
-                             "sample": timed[-1]["sample"]},
-            "e2e": {"value": round(v, 2), "unit": "s", "h2d_bytes_per_step": 0,
+            "ms_per_step": round(1e3 * v, 2), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": inst_desc, "precision": args.precision, "tol": TOL,
+                       "r0": wl["r0"], "r_cap": wl["r_cap"], "parallelism": f"replicas{world}",
+                       "l2": "host run"},
+            "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": oracle_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
@@ -686,11 +758,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus_unit")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default=None,
+                    help="default: the workload's own (FP64 for the ER configuration, "
+                         "mixed for the others)")
     ap.add_argument("--time-limit", type=float, default=600.0)
-    ap.add_argument("--cpu-budget", type=float, default=30.0)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="run every solve kernel by kernel (kernel timing on) instead of "
+                         "from CUDA graphs: for profilers")
     ap.add_argument("--no-tol2", action="store_true",
                     help="skip the extra solve at KKT 5e-6 (objective check)")
     ap.add_argument("--kernel", choices=["grad", "change"], default=None,
@@ -708,6 +784,8 @@ def main():
                     help="batching mode: the fused operator of many instances in one launch")
     ap.add_argument("--batch-count", type=int, default=1024)
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = WORKLOADS[args.workload].get("precision", "mixed")
     world, rank = dist_setup(args.gpus)
     if args.kernel:
         if rank == 0:
