@@ -197,6 +197,30 @@ hallar_status hallar_value_change(hallar_t h, const void* X, const void* Y, int3
 hallar_status hallar_trim_rank(hallar_t h, const void* Y, int32_t r, int32_t k, void* Yout,
                                double* eigs);
 
+/* Goemans-Williamson hyperplane rounding of a Max-Cut factor (not in the
+ * paper, which stops at the SDP solution; the standard way to turn the
+ * Max-Cut SDP's X = UU^T into a cut).  For each trial t the caller's normal
+ * g_t gives x_i = sign(<U_i, g_t>) (+1 at zero, in double), and the trial's
+ * cut value is -x^T C x (= (1/4) x^T L x, the weight of the cut edges, for
+ * C = -L/4).
+ *   U      [n x r] factor (host or device, the handle's precision), 1 <= r <= 256.
+ *   G      [trials x r] doubles, row t the normal of trial t (host or device).
+ *   x_best [n] int8 out (host or device, may be NULL): the best trial's signs.
+ *   cuts   [trials] doubles out (host): each trial's cut value.
+ * HALLAR_EINVAL for a handle that is not HALLAR_DIAG. */
+hallar_status hallar_maxcut_round(hallar_t h, const void* U, int32_t r, const double* G,
+                                  int32_t trials, int8_t* x_best, double* cuts);
+
+/* Entries of X = UU^T at index pairs, X_ab = <U_a, U_b> (double).  For a
+ * matrix-completion problem (HALLAR_OBSERVED, eq. matcomp-sdp) the
+ * recovered matrix is X's off-diagonal block: M^_ij = X_{i, n1 + j}.
+ *   U       [n x r] factor (host or device), 1 <= r <= 256.
+ *   a, b    [count] int32 row indices in [0, n) (host or device; host pairs
+ *           are range-checked, device pairs are the caller's to keep in range).
+ *   out     [count] doubles (host or device). */
+hallar_status hallar_factor_entries(hallar_t h, const void* U, int32_t r, const int32_t* a,
+                                    const int32_t* b, int64_t count, double* out);
+
 /* Minimum eigenpair of G = C + A*(p') (Alg. 1 step 7, eq. Grad X Space) by
  * Lanczos in FP64 with partial reorthogonalisation (the basis is swept
  * against when Simon's estimate of the loss of orthogonality passes

@@ -723,3 +723,28 @@ def trim_rank(Y, r_cap):
     Gm = Y.T @ Y
     w, Q = np.linalg.eigh(Gm)
     return Y @ Q[:, ::-1][:, :r_cap]
+
+
+# ----------------------------------------------------------------------------
+# consumers of a solved factor (not in the paper)
+# ----------------------------------------------------------------------------
+
+
+def maxcut_round(inst, U, G):
+    """Goemans-Williamson hyperplane rounding of a Max-Cut factor (not in the
+    paper, which stops at the SDP solution).  For each normal g (a row of
+    G): x = sign(U g) with sign(0) = +1, and its cut value -x^T C x, which is
+    (1/4) x^T L x, the weight of the edges x cuts, for C = -L/4.
+    Returns (cuts [trials], X [trials x n] of +-1)."""
+    U = np.asarray(U, dtype=np.float64)
+    G = np.atleast_2d(np.asarray(G, dtype=np.float64))
+    X = np.where(U @ G.T < 0.0, -1.0, 1.0).T
+    cuts = np.array([-cost_dot(inst, x[:, None]) for x in X])
+    return cuts, X
+
+
+def factor_entries(U, a, b):
+    """X_ab = <U_a, U_b> for listed index pairs (X = UU^T); for matrix
+    completion (eq. matcomp-sdp) the recovered matrix is M^_ij = X_{i, n1+j}."""
+    U = np.asarray(U, dtype=np.float64)
+    return _pair_dots_mixed(U, U, np.asarray(a, dtype=np.int64), np.asarray(b, dtype=np.int64))

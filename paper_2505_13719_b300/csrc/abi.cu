@@ -749,6 +749,77 @@ hallar_status hallar_trim_rank(hallar_t h, const void* Y, int32_t r, int32_t k, 
   });
 }
 
+hallar_status hallar_maxcut_round(hallar_t h, const void* U, int32_t r, const double* G,
+                                  int32_t trials, int8_t* x_best, double* cuts) {
+  return guarded(h, [&]() -> hallar_status {
+    Ctx* c = h;
+    if (c->P.api_family != HALLAR_DIAG)
+      fail(HALLAR_EINVAL, "hallar_maxcut_round: needs a HALLAR_DIAG (Max-Cut) problem");
+    if (!U || !G || !cuts || r < 1 || r > 256 || trials < 1)
+      fail(HALLAR_EINVAL, "hallar_maxcut_round: bad argument");
+    const int ld = padded_ld(c, r);
+    const int64_t n = c->P.n;
+    const void* Ud = stage_factor(c, U, r, ld);
+    const double* Gd = stage_dvec(c, G, (int64_t)trials * r, &c->stage_m1, &c->stage_m1_bytes);
+    int8_t* xs = (int8_t*)ensure_buffer(c, &c->stage_x, &c->stage_x_bytes, 2 * (size_t)n);
+    int8_t* xcur = xs;
+    int8_t* xbest = xs + n;
+    double best = -INFINITY;
+    for (int t = 0; t < trials; ++t) {
+      launch_round_sign(c, Ud, ld, r, Gd + (size_t)t * r, xcur);
+      launch_cut(c, xcur, S_SCALE);
+      fetch_scalars(c, S_SCALE, 2);
+      const double sx = c->h_scal[S_SCALE + 1];
+      cuts[t] = -(c->h_scal[S_SCALE] + c->P.C_J * sx * sx);
+      if (cuts[t] > best) {
+        best = cuts[t];
+        std::swap(xcur, xbest);
+      }
+    }
+    if (x_best)
+      HL_CUDA(cudaMemcpyAsync(x_best, xbest, (size_t)n,
+                              is_device_ptr(x_best) ? cudaMemcpyDeviceToDevice
+                                                    : cudaMemcpyDeviceToHost,
+                              c->stream));
+    sync(c);
+    return HALLAR_OK;
+  });
+}
+
+hallar_status hallar_factor_entries(hallar_t h, const void* U, int32_t r, const int32_t* a,
+                                    const int32_t* b, int64_t count, double* out) {
+  return guarded(h, [&]() -> hallar_status {
+    Ctx* c = h;
+    if (!U || !a || !b || !out || r < 1 || r > 256 || count < 0)
+      fail(HALLAR_EINVAL, "hallar_factor_entries: bad argument");
+    if (count == 0) return HALLAR_OK;
+    const int ld = padded_ld(c, r);
+    const int64_t n = c->P.n;
+    const void* Ud = stage_factor(c, U, r, ld);
+    // index pairs and the output on the device
+    const size_t pb = (size_t)count * sizeof(int32_t);
+    char* buf = (char*)ensure_buffer(c, &c->stage_pairs, &c->stage_pairs_bytes,
+                                     2 * pb + (size_t)count * sizeof(double));
+    const int32_t* ad = a;
+    const int32_t* bd = b;
+    if (!is_device_ptr(a) || !is_device_ptr(b)) {
+      // host pairs: validated here, then copied
+      for (int64_t t = 0; t < count; ++t)
+        if (a[t] < 0 || a[t] >= n || b[t] < 0 || b[t] >= n)
+          fail(HALLAR_EINVAL, "hallar_factor_entries: index out of range");
+      HL_CUDA(cudaMemcpyAsync(buf, a, pb, cudaMemcpyHostToDevice, c->stream));
+      HL_CUDA(cudaMemcpyAsync(buf + pb, b, pb, cudaMemcpyHostToDevice, c->stream));
+      ad = (const int32_t*)buf;
+      bd = (const int32_t*)(buf + pb);
+    }
+    double* od = is_device_ptr(out) ? out : (double*)(buf + 2 * pb);
+    launch_entries(c, Ud, ld, r, ad, bd, count, od);
+    if (od != out) copy_out_dvec(c, out, od, count);
+    sync(c);
+    return HALLAR_OK;
+  });
+}
+
 hallar_status hallar_min_eig(hallar_t h, const double* pshift, double tol, int32_t kmax,
                              const double* v0, double* lambda_min, double* v, int32_t* iters,
                              double* resid) {

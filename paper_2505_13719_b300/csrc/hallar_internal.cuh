@@ -205,6 +205,8 @@ struct hallar_ctx {
   void* stage_T = nullptr; size_t stage_T_bytes = 0;     // constraint values in the factor type
   void* stage_y = nullptr; size_t stage_y_bytes = 0;     // second factor (value change, trim)
   double* stage_vc = nullptr; size_t stage_vc_bytes = 0; // r_Y of hallar_value_change
+  void* stage_x = nullptr; size_t stage_x_bytes = 0;     // sign vectors (rounding)
+  void* stage_pairs = nullptr; size_t stage_pairs_bytes = 0;  // index pairs, entries
   void* eig_stage = nullptr; size_t eig_stage_bytes = 0;
   void* gram_part = nullptr; size_t gram_part_bytes = 0;
   void* trim_gram = nullptr; size_t trim_gram_bytes = 0;
@@ -391,6 +393,13 @@ void launch_fista_ctl(Ctx* c, LoopCtl* L);         // ADAP-FISTA steps 2-5 after
 void launch_aipp_ctl(Ctx* c, LoopCtl* L);          // ADAP-AIPP steps 2-3 after a call
 void launch_loop_x(Ctx* c, int ld, LoopCtl* L);    // x / x~ updates (XInd of L)
 void launch_trace_fix_ind(Ctx* c, const TraceInd* ti, double add);  // dst[m-1] = S_PRE[0] + add
+
+// consumers of a solved factor (consumers.cu): x = sign(U g) (int8, +1 at
+// 0); S[slot] = x^T C x without the C_J part, S[slot+1] = sum x; X_ab at pairs
+void launch_round_sign(Ctx* c, const void* U, int ld, int r, const double* g, int8_t* x);
+void launch_cut(Ctx* c, const int8_t* x, int slot);
+void launch_entries(Ctx* c, const void* U, int ld, int r, const int32_t* a, const int32_t* b,
+                    int64_t count, double* out);
 
 // solver (solver.cu)
 hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_result* res);

@@ -24,7 +24,8 @@ HALLAR_FP64, HALLAR_MIXED = 0, 1
 FAMILY = {"diag": HALLAR_DIAG, "edge": HALLAR_EDGE, "observed": HALLAR_OBSERVED}
 
 EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_grad",
-            "hallar_value_change", "hallar_trim_rank", "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
+            "hallar_value_change", "hallar_trim_rank", "hallar_maxcut_round",
+            "hallar_factor_entries", "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
             "hallar_destroy", "hallar_last_error", "hallar_status_string", "hallar_profile",
             "hallar_profile_sampling", "hallar_grad_diag_noalloc", "hallar_solve_footprint", "hallar_server_create",
             "hallar_server_submit", "hallar_server_wait", "hallar_server_get_stats",
@@ -100,6 +101,8 @@ def _load():
         "hallar_grad": ([P, P, I32, P, D, P, P, P], C.c_int),
         "hallar_value_change": ([P, P, P, I32, P, D, P, P, P], C.c_int),
         "hallar_trim_rank": ([P, P, I32, I32, P, P], C.c_int),
+        "hallar_maxcut_round": ([P, P, I32, P, I32, P, P], C.c_int),
+        "hallar_factor_entries": ([P, P, I32, P, P, I64, P], C.c_int),
         "hallar_min_eig": ([P, P, D, I32, P, P, P, P, P], C.c_int),
         "hallar_solve": ([P, P, I32, P, P], C.c_int),
         "hallar_get_solution": ([P, P, I32, P, P], C.c_int),
@@ -241,6 +244,23 @@ def hallar_value_change(h, X, Y, r, p, beta, rX=None, rY=None):
 def hallar_trim_rank(h, Y, r, k, Yout, eigs=None):
     """Yout = Y Q_k (k leading Gram eigenvectors); eigs (host float64 [r]) optional."""
     return _check(_lib.hallar_trim_rank(h, _ptr(Y), int(r), int(k), _ptr(Yout), _ptr(eigs)), h)
+
+
+def hallar_maxcut_round(h, U, r, G, x_best=None):
+    """Hyperplane rounding with the normals G [trials x r]; returns the
+    per-trial cut values (x_best, int8 [n], receives the best signs)."""
+    G = np.ascontiguousarray(G, dtype=np.float64) if isinstance(G, np.ndarray) else G
+    trials = int(G.shape[0])
+    cuts = np.empty(trials)
+    _check(_lib.hallar_maxcut_round(h, _ptr(U), int(r), _ptr(G), trials, _ptr(x_best),
+                                    _ptr(cuts)), h)
+    return cuts
+
+
+def hallar_factor_entries(h, U, r, a, b, out):
+    """out[t] = <U_a[t], U_b[t]> (int32 index arrays, host or device)."""
+    return _check(_lib.hallar_factor_entries(h, _ptr(U), int(r), _ptr(a), _ptr(b),
+                                             int(len(a)), _ptr(out)), h)
 
 
 def hallar_min_eig(h, pshift, tol, kmax, v0=None, v=None):
