@@ -155,62 +155,86 @@ def serve_requests(count, nmin, nmax, seed):
 
 
 def run_serve(args):
+    """The serving configuration: a Poisson stream of solve requests (rate
+    args.serve_rate for args.serve_seconds) served by hallar_server_* under
+    an HBM budget, then args.serve_drain seconds to finish; requests still
+    queued or running at the deadline are not served.  Each request is a
+    problem from a generated pool (families in thirds, n log-uniform) with
+    a start factor of its own.  Only solves that reach the tolerance count
+    as served; latencies are submit-to-completion of those solves.  The same
+    stream is then served by FP64 solves one at a time."""
     import torch  # noqa: F401  (initialises the CUDA context like the other modes)
 
     from paper_2505_13719_b300 import hallar as H
 
-    reqs = serve_requests(args.serve_requests, args.serve_nmin, args.serve_nmax, 5)
+    t0 = time.perf_counter()
+    pool = [inst for inst, _ in serve_requests(args.serve_pool, args.serve_nmin,
+                                                args.serve_nmax, 5)]
+    gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(6)
-    gaps = rng.exponential(1.0 / args.serve_rate, size=len(reqs))
+    count = int(round(args.serve_rate * args.serve_seconds))
+    gaps = rng.exponential(1.0 / args.serve_rate, size=count)
+    picks = rng.integers(0, len(pool), size=count)
     opts = dict(tol=TOL, r_cap=64, time_limit_s=args.time_limit)
 
     def serve(precision, inflight):
-        statuses = []
+        dt = np.float32 if precision == H.HALLAR_MIXED else np.float64
+        statuses, lats, fams = [], [], []
         with H.Server(args.serve_budget_gb * 1e9, inflight) as srv:
             t0 = time.perf_counter()
             tickets, due = [], 0.0
-            for (inst, U0), gap in zip(reqs, gaps):   # Poisson arrivals
+            for k, (gap, pi) in enumerate(zip(gaps, picks)):   # Poisson arrivals
                 due += gap
                 wait = due - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(wait)
-                tickets.append(srv.submit(inst, U0, precision, **opts))
-            lats = []
-            for t in tickets:
-                st, res, U, p, lat = srv.wait(t)
+                inst = pool[pi]
+                U0 = I.initial_factor(inst.n, 2, 1000 + k).astype(dt)
+                tickets.append((srv.submit(inst, U0, precision, **opts), inst.family))
+            deadline = t0 + args.serve_seconds + args.serve_drain
+            for t, fam in tickets:
+                left = deadline - time.perf_counter()
+                st, res, U, p, lat = srv.wait(t, max(left, 0.0))
+                if res is None:  # still queued or running at the deadline
+                    break
                 statuses.append(int(st))
                 lats.append(lat)
-            wall = time.perf_counter() - t0
+                fams.append(fam)
+            wall = min(time.perf_counter(), deadline) - t0
             stats = srv.stats()
-        ok = statuses.count(H.HALLAR_OK)
-        ok_lat = sorted(l for l, st in zip(lats, statuses) if st == H.HALLAR_OK)
+        ok = [i for i, st in enumerate(statuses) if st == H.HALLAR_OK]
+        ok_lat = sorted(lats[i] for i in ok)
         pct = (lambda q: round(float(np.percentile(ok_lat, q)), 4)) if ok_lat else (lambda q: None)
-        return {"solves_per_s": round(ok / wall, 4), "wall_s": round(wall, 3),
-                "requests": len(reqs), "converged": ok,
+        by_fam = {f: sum(1 for i in ok if fams[i] == f) for f in ("diag", "edge", "observed")}
+        return {"solves_per_s": round(len(ok) / wall, 4), "wall_s": round(wall, 3),
+                "requests": count, "completed_by_deadline": len(statuses),
+                "converged": len(ok), "converged_by_family": by_fam,
                 "time_limit_stops": statuses.count(H.HALLAR_ETIMEOUT),
-                "other_stops": len(statuses) - ok - statuses.count(H.HALLAR_ETIMEOUT),
+                "other_stops": len(statuses) - len(ok) - statuses.count(H.HALLAR_ETIMEOUT),
+                "not_served_by_deadline": count - len(statuses),
                 "p50_s": pct(50), "p99_s": pct(99),
-                "p50_s_all_requests": round(stats["p50_latency_s"], 4),
-                "p99_s_all_requests": round(stats["p99_latency_s"], 4),
                 "max_inflight_seen": int(stats["max_inflight_seen"]),
-                "peak_gb": round(stats["peak_bytes_inflight"] / 1e9, 3),
-                "statuses": statuses}
+                "peak_gb": round(stats["peak_bytes_inflight"] / 1e9, 3)}
 
     served = serve(H.HALLAR_MIXED, args.serve_inflight)
     one_fp64 = serve(H.HALLAR_FP64, 1)
-    ns = sorted(inst.n for inst, _ in reqs)
+    ns = sorted(inst.n for inst in pool)
     return {
         "metric": SERVE_METRIC, "value": served["solves_per_s"], "unit": "solves/s",
         "n_gpus": 1, "higher_is_better": True, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving mix: Max-Cut ER (avg deg 8), theta G(n,5n), "
                                "completion n1=n2=n/2 rank 3; thirds",
-                   "requests": len(reqs), "n_range": [args.serve_nmin, args.serve_nmax],
-                   "n_median": ns[len(ns) // 2], "rate_per_s": args.serve_rate,
+                   "pool": len(pool), "pool_generation_s": round(gen_s, 1),
+                   "requests": count, "n_range": [args.serve_nmin, args.serve_nmax],
+                   "n_median_pool": ns[len(ns) // 2], "rate_per_s": args.serve_rate,
+                   "arrival_s": args.serve_seconds, "drain_s": args.serve_drain,
+                   "per_request_time_limit_s": args.time_limit,
                    "max_inflight": args.serve_inflight, "hbm_budget_gb": args.serve_budget_gb,
                    "tol": TOL, "r_cap": 64},
         "p50_s": served["p50_s"], "p99_s": served["p99_s"], "served_mixed": served,
         "fp64_one_at_a_time": one_fp64,
-        "speedup_solves_per_s": round(served["solves_per_s"] / one_fp64["solves_per_s"], 3),
+        "speedup_solves_per_s": (round(served["solves_per_s"] / one_fp64["solves_per_s"], 3)
+                                 if one_fp64["solves_per_s"] else None),
     }
 
 
@@ -323,6 +347,67 @@ def run_batch(args):
                      "note": "whole batched call: p/beta conversion, the row kernel, the "
                              "per-instance reduction"},
     }
+
+
+# ---------------------------------------------------------------------------
+# the hypercube theta reproduction: theta(Q_d) = 2^(d-1)
+# ---------------------------------------------------------------------------
+HYPERCUBE_METRIC = "time to 1e-5 KKT of the Lovasz theta SDP on hypercubes H(d,2), 1 B300"
+# the paper's cuHALLaR times (s, on-the-fly generation / HSLR input) on an
+# H200 in FP64 (Table tab:reduced_hamming_graphs): context, another machine
+PAPER_HAMMING_S = {10: (1.735, 0.798), 11: (1.627, 0.92), 12: (2.033, 1.83), 13: (3.106, 1.10),
+                   14: (3.170, 1.28), 15: (3.223, 2.701), 16: (4.457, 3.83), 17: (3.904, 2.51),
+                   18: (2.627, 3.43), 19: (5.281, 10.70), 20: (8.109, 6.62),
+                   21: (16.966, 12.96), 22: (37.145, 18.842), 23: (83.905, 51.75)}
+
+
+def run_hypercube(args):
+    """theta(Q_d) for d in [d_lo, d_hi] (Section 5.3, eq. lovasz; Q_d is
+    bipartite, so theta = alpha = 2^(d-1)): one solve per d after one
+    untimed warm-up solve, the problem resident in HBM, CUDA events on the
+    solve's stream."""
+    import torch
+
+    from paper_2505_13719_b300 import hallar as H
+
+    prec = H.HALLAR_MIXED if args.precision == "mixed" else H.HALLAR_FP64
+    dt = np.float32 if prec == H.HALLAR_MIXED else np.float64
+    stream = torch.cuda.current_stream()
+    rows = []
+    for d in range(args.hypercube[0], args.hypercube[1] + 1):
+        t0 = time.perf_counter()
+        inst = I.theta(1 << d, *I.hypercube_graph(d))
+        gen_s = time.perf_counter() - t0
+        U0 = torch.from_numpy(I.initial_factor(inst.n, 2, 7).astype(dt)).cuda()
+        t0 = time.perf_counter()
+        hd = H.create_from_instance(inst, prec, tol=TOL, r_cap=64, time_limit_s=args.time_limit,
+                                    stream=stream.cuda_stream)
+        create_s = time.perf_counter() - t0
+        H.hallar_solve(hd.h, U0, 2)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, res = H.hallar_solve(hd.h, U0, 2)
+        e1.record(stream)
+        e1.synchronize()
+        hd.close()
+        exact = float(1 << (d - 1))
+        paper = PAPER_HAMMING_S.get(d)
+        rows.append({"d": d, "n": inst.n, "edges": int(inst.meta["edges"]),
+                     "time_s": round(e0.elapsed_time(e1) / 1e3, 4), "status": int(st),
+                     "kkt": res.kkt, "theta": -res.pval, "exact": exact,
+                     "rel_err": abs(-res.pval - exact) / exact, "rank": res.rank,
+                     "grad_evals": int(res.grad_evals), "lanczos_iters": int(res.lanczos_iters),
+                     "generate_s": round(gen_s, 2), "create_s": round(create_s, 3),
+                     "paper_h200_fp64_s": paper[0] if paper else None,
+                     "paper_h200_fp64_hslr_s": paper[1] if paper else None})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return {"metric": HYPERCUBE_METRIC, "unit": "s", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f32+f64" if prec == H.HALLAR_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": "Lovasz theta SDP on the hypercubes Q_d = H(d,2), trace row",
+                       "precision": args.precision, "tol": TOL, "r0": 2, "r_cap": 64},
+            "rows": rows,
+            "note": "paper times: cuHALLaR on an H200 in FP64, context only"}
 
 
 # ---------------------------------------------------------------------------
@@ -664,16 +749,33 @@ def oracle_threads():
     return os.cpu_count() or 1
 
 
+class _BlasThreads:
+    """BLAS thread limit for the oracle (threadpoolctl when it is present;
+    otherwise the BLAS library's own default, which is every core)."""
+
+    def __init__(self, n):
+        try:
+            from threadpoolctl import threadpool_limits
+            self.ctx = threadpool_limits(limits=n)
+        except ImportError:
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        if self.ctx is not None:
+            self.ctx.__exit__(*a)
+
+
 def oracle_sample_solve(smp):
     """The oracle's own full solve (its own trajectory, FP64) of the
     workload's bounded sample to the bench tolerance; returns (seconds,
     result)."""
-    from threadpoolctl import threadpool_limits
-
     from oracle import hallar_oracle as O
     sinst = smp["make"]()
     U0 = I.initial_factor(sinst.n, smp["r0"], smp["u0_seed"])
-    with threadpool_limits(limits=oracle_threads()):
+    with _BlasThreads(oracle_threads()):
         t0 = time.perf_counter()
         res = O.hallar_solve(sinst, U0, opt=O.Options(tol=TOL, r_cap=smp["r_cap"]))
         return time.perf_counter() - t0, res
@@ -683,11 +785,9 @@ def cpu_baseline(wl, inst, rank):
     """The FP64 oracle as it stands, on the host cores: its own full solve of
     the workload's bounded sample (nothing projected, no count from the GPU
     path), and its per-operator times at the workload's full size."""
-    from threadpoolctl import threadpool_limits
-
     from oracle import hallar_oracle as O
     out = {"value": None, "unit": "s", "cores": oracle_threads(), "kind": "oracle"}
-    with threadpool_limits(limits=oracle_threads()):
+    with _BlasThreads(oracle_threads()):
         rng = np.random.default_rng(0)
         r = max(2, rank)
         U = rng.standard_normal((inst.n, r)) / math.sqrt(r)
@@ -774,15 +874,20 @@ def main():
     ap.add_argument("--rank", type=int, default=10, help="factor width for --kernel")
     ap.add_argument("--serve", action="store_true",
                     help="serving mode: a Poisson stream of mixed solves through hallar_server")
-    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-pool", type=int, default=96, help="generated problems")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window")
+    ap.add_argument("--serve-drain", type=float, default=120.0,
+                    help="seconds after the arrival window to finish")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="arrivals per second")
     ap.add_argument("--serve-nmin", type=int, default=1000)
-    ap.add_argument("--serve-nmax", type=int, default=20000)
-    ap.add_argument("--serve-inflight", type=int, default=8)
+    ap.add_argument("--serve-nmax", type=int, default=200000)
+    ap.add_argument("--serve-inflight", type=int, default=32)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--batch", action="store_true",
                     help="batching mode: the fused operator of many instances in one launch")
     ap.add_argument("--batch-count", type=int, default=1024)
+    ap.add_argument("--hypercube", type=int, nargs=2, metavar=("D_LO", "D_HI"), default=None,
+                    help="theta on the hypercubes Q_d for d in [D_LO, D_HI]")
     args = ap.parse_args()
     if args.precision is None:
         args.precision = WORKLOADS[args.workload].get("precision", "mixed")
@@ -798,6 +903,10 @@ def main():
     if args.batch:
         if rank == 0:
             print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.hypercube:
+        if rank == 0:
+            print(json.dumps(run_hypercube(args)), flush=True)
         return
     if args.impl == "reference":
         line = run_reference(args, world, rank)

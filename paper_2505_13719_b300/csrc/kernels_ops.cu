@@ -173,77 +173,106 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AI
 
     const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
     T cdot_l = (T)0;  // lane part of <U_i, sum_j C_ij U_j> over the C entries
-    // Edges go in batches: lane t of the group loads the column, value and
-    // code of edge eb + t with one instruction and a shuffle hands them to the
-    // group, so a row's metadata costs one load round trip per batch instead
-    // of one per edge ahead of each gather.
-    for (int eb = e0; eb < e1; eb += kEdgeBatch<G>) {
-      const int cnt = min(kEdgeBatch<G>, e1 - eb);
-      int col_t = 0, code_t = 0;
-      T cv_t = (T)0;
-      if (lane_g < cnt) {
-        col_t = a.col[eb + lane_g];
-        if (Tr::kCval) cv_t = cval[eb + lane_g];
-        if (Tr::kPairs) code_t = a.code[eb + lane_g];
+    // one merged entry (column j, C value cv, constraint code cd) with the
+    // gathered row U_j
+    auto apply_edge = [&](const T (&uj)[K][VEC], T cv, int cd) {
+      T coef;
+      bool is_c;
+      if (Tr::kDiag) {
+        coef = cv;
+        is_c = true;
+      } else {
+        is_c = Tr::kCval && cd == kNoCons;
+        if (is_c) {
+          coef = cv;
+        } else {
+          // pair constraint l: A_l . UU^T = <U_i, U_j>
+          T d_l = (T)0;
+#pragma unroll
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) d_l = tfma(u[k][v], uj[k][v], d_l);
+          const T dot = group_sum<G>(d_l, gmask);
+          const bool owner = cd >= 0;
+          const int l = owner ? cd : -cd - 1;
+          const T r = dot - bv[l];
+          const T pl = pv[l];
+          const T ps = tfma(beta, r, pl);
+          coef = (T)0.5 * ps;
+          if (owner && lane_g == 0) {
+            acc_pr.add(pl * r);
+            acc_rr.add(r * r);
+            acc_mag.add(tabs(ps) * tabs(dot));
+            if (resid) resid[l] = r;
+            if (Tout) Tout[l] = dot;
+          }
+        }
       }
 #pragma unroll
-      for (int t = 0; t < kEdgeBatch<G>; ++t) {
-        const T cv = Tr::kCval ? group_bcast<G>(cv_t, t, gmask) : (T)0;
-        const int cd = Tr::kPairs ? group_bcast<G>(code_t, t, gmask) : 0;
-        const int64_t j = group_bcast<G>(col_t, t, gmask);
-        if (t >= cnt) continue;  // uniform over the group
-        T uj[K][VEC];
+      for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const int ch = lane_g + k * G;
-          if (ch < nch) {
-            load_chunk<T>(U, j * a.ld + ch * VEC, uj[k]);
-          } else {
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) uj[k][v] = (T)0;
-          }
+        for (int v = 0; v < VEC; ++v) {
+          // (diagonal family: acc holds only C terms; its dot with U_i is
+          // taken once after the loop)
+          if (!Tr::kDiag && is_c) cdot_l = tfma(coef * u[k][v], uj[k][v], cdot_l);
+          acc[k][v] = tfma(coef, uj[k][v], acc[k][v]);
         }
-        T coef;
-        bool is_c;
-        if (Tr::kDiag) {
-          coef = cv;
-          is_c = true;
+    };
+    auto gather = [&](int64_t j, T (&uj)[K][VEC]) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int ch = lane_g + k * G;
+        if (ch < nch) {
+          load_chunk<T>(U, j * a.ld + ch * VEC, uj[k]);
         } else {
-          is_c = Tr::kCval && cd == kNoCons;
-          if (is_c) {
-            coef = cv;
-          } else {
-            // pair constraint l: A_l . UU^T = <U_i, U_j>
-            T d_l = (T)0;
 #pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) d_l = tfma(u[k][v], uj[k][v], d_l);
-            const T dot = group_sum<G>(d_l, gmask);
-            const bool owner = cd >= 0;
-            const int l = owner ? cd : -cd - 1;
-            const T r = dot - bv[l];
-            const T pl = pv[l];
-            const T ps = tfma(beta, r, pl);
-            coef = (T)0.5 * ps;
-            if (owner && lane_g == 0) {
-              acc_pr.add(pl * r);
-              acc_rr.add(r * r);
-              acc_mag.add(tabs(ps) * tabs(dot));
-              if (resid) resid[l] = r;
-              if (Tout) Tout[l] = dot;
-            }
-          }
+          for (int v = 0; v < VEC; ++v) uj[k][v] = (T)0;
+        }
+      }
+    };
+    if constexpr (G == 1) {
+      // one thread per row: entries two at a time, both gathers issued before
+      // either is used, so a row's chain of dependent loads is half as long
+      int e = e0;
+      for (; e + 2 <= e1; e += 2) {
+        const int64_t j0 = a.col[e], j1 = a.col[e + 1];
+        const T cv0 = Tr::kCval ? cval[e] : (T)0, cv1 = Tr::kCval ? cval[e + 1] : (T)0;
+        const int cd0 = Tr::kPairs ? a.code[e] : 0, cd1 = Tr::kPairs ? a.code[e + 1] : 0;
+        T uj0[K][VEC], uj1[K][VEC];
+        gather(j0, uj0);
+        gather(j1, uj1);
+        apply_edge(uj0, cv0, cd0);
+        apply_edge(uj1, cv1, cd1);
+      }
+      if (e < e1) {
+        T uj0[K][VEC];
+        gather(a.col[e], uj0);
+        apply_edge(uj0, Tr::kCval ? cval[e] : (T)0, Tr::kPairs ? a.code[e] : 0);
+      }
+    } else {
+      // Edges go in batches: lane t of the group loads the column, value and
+      // code of edge eb + t with one instruction and a shuffle hands them to
+      // the group, so a row's metadata costs one load round trip per batch
+      // instead of one per edge ahead of each gather.
+      for (int eb = e0; eb < e1; eb += kEdgeBatch<G>) {
+        const int cnt = min(kEdgeBatch<G>, e1 - eb);
+        int col_t = 0, code_t = 0;
+        T cv_t = (T)0;
+        if (lane_g < cnt) {
+          col_t = a.col[eb + lane_g];
+          if (Tr::kCval) cv_t = cval[eb + lane_g];
+          if (Tr::kPairs) code_t = a.code[eb + lane_g];
         }
 #pragma unroll
-        for (int k = 0; k < K; ++k)
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            // (diagonal family: acc holds only C terms; its dot with U_i is
-            // taken once after the loop)
-            if (!Tr::kDiag && is_c) cdot_l = tfma(coef * u[k][v], uj[k][v], cdot_l);
-            acc[k][v] = tfma(coef, uj[k][v], acc[k][v]);
-          }
+        for (int t = 0; t < kEdgeBatch<G>; ++t) {
+          const T cv = Tr::kCval ? group_bcast<G>(cv_t, t, gmask) : (T)0;
+          const int cd = Tr::kPairs ? group_bcast<G>(code_t, t, gmask) : 0;
+          const int64_t j = group_bcast<G>(col_t, t, gmask);
+          if (t >= cnt) continue;  // uniform over the group
+          T uj[K][VEC];
+          gather(j, uj);
+          apply_edge(uj, cv, cd);
+        }
       }
     }
     if (Tr::kDiag) {
@@ -423,56 +452,99 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
     }
     const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
     T cd_l = (T)0;
-    // edge metadata in batches, as in k_grad
-    for (int eb = e0; eb < e1; eb += kEdgeBatch<G>) {
-      const int cnt = min(kEdgeBatch<G>, e1 - eb);
-      int col_t = 0, code_t = 0;
-      T cv_t = (T)0;
-      if (lane_g < cnt) {
-        col_t = a.col[eb + lane_g];
-        if (Tr::kCval) cv_t = cval[eb + lane_g];
-        if (Tr::kPairs) code_t = a.code[eb + lane_g];
-      }
+    // gathered rows X_j and Y_j (Y_j = cs Z_j in the YZ form)
+    auto gather = [&](int64_t j, T (&xj)[K][VEC], T (&yj)[K][VEC]) {
 #pragma unroll
-      for (int t = 0; t < kEdgeBatch<G>; ++t) {
-        const T cv = Tr::kCval ? group_bcast<G>(cv_t, t, gmask) : (T)0;
-        const int cd = Tr::kPairs ? group_bcast<G>(code_t, t, gmask) : 0;
-        const int64_t j = group_bcast<G>(col_t, t, gmask);
-        if (t >= cnt) continue;  // uniform over the group
-        if (Tr::kPairs) {
-          if (cd < 0 && cd != kNoCons) continue;  // mirrored pair entry: the owner row does it
-          if (!Tr::kCval && cd == kNoCons) continue;
-        }
-        T pd = (T)0;  // lane part of <D_i, Y_j> + <X_i, D_j>
+      for (int k = 0; k < K; ++k) {
+        const int ch = lane_g + k * G;
+        if (ch < nch) {
+          load_chunk<T>(X, j * a.ld + ch * VEC, xj[k]);
+          load_chunk<T>(Yv, j * a.ld + ch * VEC, yj[k]);
+          if constexpr (YZ) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const int ch = lane_g + k * G;
-          if (ch < nch) {
-            T xj[VEC], yj[VEC];
-            load_chunk<T>(X, j * a.ld + ch * VEC, xj);
-            load_chunk<T>(Yv, j * a.ld + ch * VEC, yj);
-            if constexpr (YZ) {
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) yj[v] = cs * yj[v];
-            }
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              pd = tfma(d[k][v], yj[v], pd);
-              pd = tfma(x[k][v], yj[v] - xj[v], pd);
-            }
+            for (int v = 0; v < VEC; ++v) yj[k][v] = cs * yj[k][v];
           }
-        }
-        if (Tr::kDiag || cd == kNoCons) {
-          cd_l = tfma(cv, pd, cd_l);
         } else {
-          // owned pair constraint l: dT_l = <Y_i,Y_j> - <X_i,X_j>
-          const T dt = group_sum<G>(pd, gmask);
-          if (lane_g == 0) {
-            const T rx = rXv[cd];
-            acc_pd.add(pv[cd] * dt);
-            acc_q.add(dt * ((T)2 * rx + dt));
-            if (rYv) rYv[cd] = rx + dt;
-          }
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) xj[k][v] = yj[k][v] = (T)0;
+        }
+      }
+    };
+    // one merged entry: <D_i, Y_j> + <X_i, D_j> weighted by its C value, or
+    // the change of an owned pair constraint
+    auto apply_edge = [&](const T (&xj)[K][VEC], const T (&yj)[K][VEC], T cv, int cd) {
+      T pd = (T)0;  // lane part of <D_i, Y_j> + <X_i, D_j>
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          pd = tfma(d[k][v], yj[k][v], pd);
+          pd = tfma(x[k][v], yj[k][v] - xj[k][v], pd);
+        }
+      if (Tr::kDiag || cd == kNoCons) {
+        cd_l = tfma(cv, pd, cd_l);
+      } else {
+        // owned pair constraint l: dT_l = <Y_i,Y_j> - <X_i,X_j>
+        const T dt = group_sum<G>(pd, gmask);
+        if (lane_g == 0) {
+          const T rx = rXv[cd];
+          acc_pd.add(pv[cd] * dt);
+          acc_q.add(dt * ((T)2 * rx + dt));
+          if (rYv) rYv[cd] = rx + dt;
+        }
+      }
+    };
+    // mirrored pair entries are done by the owner row; pure C entries only
+    // in families with a sparse C
+    auto skip = [&](int cd) {
+      if (!Tr::kPairs) return false;
+      return (cd < 0 && cd != kNoCons) || (!Tr::kCval && cd == kNoCons);
+    };
+    if constexpr (G == 1) {
+      // one thread per row: entries two at a time, all gathers issued before
+      // any is used
+      int e = e0;
+      for (; e + 2 <= e1; e += 2) {
+        const int cd0 = Tr::kPairs ? a.code[e] : 0, cd1 = Tr::kPairs ? a.code[e + 1] : 0;
+        const bool s0 = skip(cd0), s1 = skip(cd1);
+        if (s0 && s1) continue;
+        const int64_t j0 = a.col[e], j1 = a.col[e + 1];
+        const T cv0 = Tr::kCval ? cval[e] : (T)0, cv1 = Tr::kCval ? cval[e + 1] : (T)0;
+        T xj0[K][VEC], yj0[K][VEC], xj1[K][VEC], yj1[K][VEC];
+        if (!s0) gather(j0, xj0, yj0);
+        if (!s1) gather(j1, xj1, yj1);
+        if (!s0) apply_edge(xj0, yj0, cv0, cd0);
+        if (!s1) apply_edge(xj1, yj1, cv1, cd1);
+      }
+      if (e < e1) {
+        const int cd0 = Tr::kPairs ? a.code[e] : 0;
+        if (!skip(cd0)) {
+          T xj0[K][VEC], yj0[K][VEC];
+          gather(a.col[e], xj0, yj0);
+          apply_edge(xj0, yj0, Tr::kCval ? cval[e] : (T)0, cd0);
+        }
+      }
+    } else {
+      // edge metadata in batches, as in k_grad
+      for (int eb = e0; eb < e1; eb += kEdgeBatch<G>) {
+        const int cnt = min(kEdgeBatch<G>, e1 - eb);
+        int col_t = 0, code_t = 0;
+        T cv_t = (T)0;
+        if (lane_g < cnt) {
+          col_t = a.col[eb + lane_g];
+          if (Tr::kCval) cv_t = cval[eb + lane_g];
+          if (Tr::kPairs) code_t = a.code[eb + lane_g];
+        }
+#pragma unroll
+        for (int t = 0; t < kEdgeBatch<G>; ++t) {
+          const T cv = Tr::kCval ? group_bcast<G>(cv_t, t, gmask) : (T)0;
+          const int cd = Tr::kPairs ? group_bcast<G>(code_t, t, gmask) : 0;
+          const int64_t j = group_bcast<G>(col_t, t, gmask);
+          if (t >= cnt) continue;  // uniform over the group
+          if (skip(cd)) continue;
+          T xj[K][VEC], yj[K][VEC];
+          gather(j, xj, yj);
+          apply_edge(xj, yj, cv, cd);
         }
       }
     }

@@ -66,6 +66,8 @@ CLOSED = [
     ("theta K6", lambda: I.theta(6, *I.complete_graph(6)), 1.0),
     ("theta empty 7", lambda: I.theta(7, np.zeros(0, int), np.zeros(0, int)), 7.0),
     ("theta H(10,2)", lambda: I.theta(1024, *I.hypercube_graph(10)), 512.0),
+    ("theta H(13,2)", lambda: I.theta(8192, *I.hypercube_graph(13)), 4096.0),
+    ("theta H(16,2)", lambda: I.theta(65536, *I.hypercube_graph(16)), 32768.0),
 ]
 
 
