@@ -365,7 +365,9 @@ void launch_dvec(Ctx* c, int op, int64_t len, double* a, const double* b, const 
 void launch_axpy_t(Ctx* c, int64_t len, double* a, const double* b, const void* t, double s);
 void launch_to_factor_type(Ctx* c, int64_t len, void* out, const double* in);
 void launch_to_double(Ctx* c, int64_t len, double* out, const void* in);
-// Gram U^T U (r x r, FP64) and out = U Q (Q row-major r x k)
+// Gram U^T U (r x r, FP64 result) and out = U Q (Q row-major r x k); the
+// mixed form's float Gram runs on the tensor cores (gram_tc.cu)
+void launch_gram_tc(Ctx* c, const void* U, int ld, int r, double* G);
 void launch_gram(Ctx* c, const void* U, int ld, int r, double* G);
 void launch_right_mult(Ctx* c, const void* U, int ld, int r, const double* Q, int k, void* out,
                        int ld_out);

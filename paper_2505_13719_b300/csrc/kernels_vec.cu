@@ -286,6 +286,12 @@ void launch_dvec(Ctx* c, int op, int64_t len, double* a, const double* b, const 
 
 void launch_gram(Ctx* c, const void* U, int ld, int r, double* G) {
   if (r * r > kGramAcc * kBlock) fail(HALLAR_EINVAL, "rank trim supports ranks up to 90");
+  // the float factor of the mixed form: on the tensor cores (gram_tc.cu);
+  // FP64 factors keep the FP64 CUDA-core sum (B300's FP64 tensor rate is low)
+  if (c->opt.precision == HALLAR_MIXED) {
+    launch_gram_tc(c, U, ld, r, G);
+    return;
+  }
   int grid = grid_for(c, c->P.n, 8 * 8);
   if (grid > 512) grid = 512;
   double* part = (double*)ensure_buffer(c, &c->gram_part, &c->gram_part_bytes,
