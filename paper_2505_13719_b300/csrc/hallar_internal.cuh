@@ -347,8 +347,11 @@ void launch_colsum_diff(Ctx* c, const void* X, const void* Y, int ld, double* sD
 void launch_colsum_ind(Ctx* c, int ld, const ColInd* cind);
 void launch_colsum_diff_ind(Ctx* c, int ld, const ColInd* cind);
 
-// r = 1 operator pieces in FP64 (Frank-Wolfe)
-void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, int slot);
+// r = 1 operator pieces in FP64 (Frank-Wolfe); resid = A(YY^T) - b (double)
+void launch_fw_denom(Ctx* c, const double* y, const double* resid, double tau2, int slot);
+// r64 = A(YY^T) - b in double from the stored factor (trace row excluded);
+// S[slot] = sum r64^2, S[slot+1] = |Y|_F^2
+void launch_resid64(Ctx* c, const void* U, int ld, int r, double* r64, int slot);
 
 // streaming kernels (kernels_vec.cu); reductions into the given slot
 void launch_pad_copy(Ctx* c, const void* src, int ld_src, void* dst, int ld_dst, int r_copy,
@@ -360,9 +363,7 @@ void launch_fw_append(Ctx* c, const void* Y, int ld, int r, const double* y, dou
 // m-length FP64 vectors: op 0: a = b + s cc; op 1: slot = <b, cc>; op 2: slot = |b|^2
 void launch_dvec(Ctx* c, int op, int64_t len, double* a, const double* b, const double* cc,
                  double s, int slot);
-// a = b + s * t with t of the factor type; conversions between double
-// vectors and factor-typed vectors
-void launch_axpy_t(Ctx* c, int64_t len, double* a, const double* b, const void* t, double s);
+// conversions between double vectors and factor-typed vectors
 void launch_to_factor_type(Ctx* c, int64_t len, void* out, const double* in);
 void launch_to_double(Ctx* c, int64_t len, double* out, const void* in);
 // Gram U^T U (r x r, FP64 result) and out = U Q (Q row-major r x k); the

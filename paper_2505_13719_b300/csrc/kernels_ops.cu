@@ -117,15 +117,26 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AI
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
   const int nch = a.ld / VEC;
-  const T beta = (T)gi.beta;
-  const T c2lam = (T)gi.c2lam, invL = (T)gi.invL, Lt = (T)gi.L;
-
-  // shifted multiplier of the trace row, identical for every row
-  T ps_tr = (T)0;
-  if (Tr::kPairs && a.has_trace) {
-    const double rt = io.pre[0] - (double)bv[a.trace_row];
-    ps_tr = (T)((double)pv[a.trace_row] + gi.beta * rt);
+  // coefficients in the factor type and the trace row's shifted multiplier
+  // (identical for every row), formed by one thread of the block: double
+  // arithmetic and conversions occupy the slow FP64 pipe
+  __shared__ T s_coef[5];
+  if (threadIdx.x == 0) {
+    s_coef[0] = (T)gi.beta;
+    s_coef[1] = (T)gi.c2lam;
+    s_coef[2] = (T)gi.invL;
+    s_coef[3] = (T)gi.L;
+    T pst = (T)0;
+    if (Tr::kPairs && a.has_trace) {
+      const double rt = io.pre[0] - (double)bv[a.trace_row];
+      pst = (T)((double)pv[a.trace_row] + gi.beta * rt);
+    }
+    s_coef[4] = pst;
   }
+  __syncthreads();
+  const T beta = s_coef[0];
+  const T c2lam = s_coef[1], invL = s_coef[2], Lt = s_coef[3];
+  const T ps_tr = s_coef[4];
 
   // C.UU^T (sparse + diagonal part), p.r, r.r, and the magnitude
   // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g;
@@ -388,11 +399,16 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
   const unsigned gmask = group_mask<G>();
   const int64_t ngroups = (int64_t)gridDim.x * (kBlock / G);
   const int nch = a.ld / VEC;
-  T cs = (T)1;
+  // the ball projection's factor, formed by one thread of the block
+  __shared__ T s_cs;
   if constexpr (YZ) {
-    const double zn = sqrt(*io.z2);
-    cs = (T)(zn > io.tau ? io.tau / zn : 1.0);
+    if (threadIdx.x == 0) {
+      const double zn = sqrt(*io.z2);
+      s_cs = (T)(zn > io.tau ? io.tau / zn : 1.0);
+    }
+    __syncthreads();
   }
+  const T cs = YZ ? s_cs : (T)1;
 
   // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT; YZ:
   // |D|^2, <D, (Y + X)/2 - centre>, |Y - centre|^2
@@ -581,17 +597,25 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
   // mode 0: s = colsum(U), scal = [|U|_F^2, |s|^2]
   // mode 1: X = U, D = Y - X: s = colsum(D), s2 = colsum(Y + X),
   //         scal = [sum <D_i, Y_i + X_i>, <s, s2>]
-  T ys = (T)1;
+  __shared__ T s_ys;
   if (cind != nullptr) {
     const ColInd ci = *cind;
     if (!ci.active) return;  // uniform over the grid
     U = static_cast<const T*>(ci.U);
     Y = static_cast<const T*>(ci.Y);
-    if (ci.y_from_z) {
-      const double zn = sqrt(*z2);
-      ys = (T)(zn > tau ? tau / zn : 1.0);
+    if (threadIdx.x == 0) {
+      T v = (T)1;
+      if (ci.y_from_z) {
+        const double zn = sqrt(*z2);
+        v = (T)(zn > tau ? tau / zn : 1.0);
+      }
+      s_ys = v;
     }
+  } else if (threadIdx.x == 0) {
+    s_ys = (T)1;
   }
+  __syncthreads();
+  const T ys = s_ys;
   __shared__ double t1[kBlock], t2[kBlock];
   __shared__ double sh[kColsumMax], sh2[kColsumMax];
   __shared__ double shr[1][kBlock / 32];
@@ -663,6 +687,48 @@ __global__ void __launch_bounds__(kBlock) k_colsum(const T* __restrict__ U, int6
     scal_out[1] = q;
     *counter = 0u;
   }
+}
+
+// ---------------------------------------------------------------------------
+// r = A(YY^T) - b in double from the stored factor (thread per row, the
+// owner entry of each pair constraint): the residuals of the dual update
+// p <- p + beta r, the Lanczos shift p + beta r, the Frank-Wolfe step and the
+// KKT primal residual.  In the mixed form the operator kernels' float
+// residuals carry rounding of order 2^-24 |Y_i||Y_j|, which beta (up to 1e8)
+// would amplify into the multipliers; here every product of the float
+// factor is exact in double.  Reduces [sum r_l^2 (trace row excluded),
+// |Y|_F^2]; the trace row's entry is left to the caller.
+// ---------------------------------------------------------------------------
+template <class T, int FAM>
+__global__ void __launch_bounds__(kBlock) k_resid64(OpArgs a, const T* __restrict__ U, int r,
+                                                    const double* __restrict__ bd,
+                                                    double* __restrict__ r64) {
+  using Tr = FamTraits<FAM>;
+  double red[2] = {0.0, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < a.n;
+       i += (int64_t)gridDim.x * kBlock) {
+    const T* ui = U + i * (int64_t)a.ld;
+    double nrm = 0.0;
+    for (int k = 0; k < r; ++k) nrm = fma((double)ui[k], (double)ui[k], nrm);
+    red[1] += nrm;
+    if (Tr::kDiag) {
+      const double rr = nrm - bd[i];
+      r64[i] = rr;
+      red[0] = fma(rr, rr, red[0]);
+    } else {
+      for (int e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+        const int cd = a.code[e];
+        if (cd < 0) continue;  // mirrored or pure C entry
+        const T* uj = U + (int64_t)a.col[e] * a.ld;
+        double dot = 0.0;
+        for (int k = 0; k < r; ++k) dot = fma((double)ui[k], (double)uj[k], dot);
+        const double rr = dot - bd[cd];
+        r64[cd] = rr;
+        red[0] = fma(rr, rr, red[0]);
+      }
+    }
+  }
+  grid_reduce<2>(red, a.partials, a.counter, a.out);
 }
 
 // ---------------------------------------------------------------------------
@@ -972,23 +1038,29 @@ void launch_colsum_diff_ind(Ctx* c, int ld, const ColInd* cind) {
                           cind);
 }
 
-void launch_fw_denom(Ctx* c, const double* y, const void* resid, double tau2, int slot) {
+void launch_fw_denom(Ctx* c, const double* y, const double* resid, double tau2, int slot) {
   OpArgs a = make_args(c, 1, slot);
   const int grid = grid_for(c, c->P.n, kBlock);
-  const bool mixed = c->opt.precision == HALLAR_MIXED;
-#define HL_FWD(FAMV)                                                                          \
-  if (mixed)                                                                                  \
-    k_fw_denom<float, FAMV><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y, (const float*)resid, \
-                                                            tau2);                            \
-  else                                                                                        \
-    k_fw_denom<double, FAMV><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y,                   \
-                                                             (const double*)resid, tau2)
   switch (c->P.fam) {
-    case FAM_DIAG: HL_FWD(FAM_DIAG); break;
-    case FAM_EDGE: HL_FWD(FAM_EDGE); break;
-    default: HL_FWD(FAM_EDGE_C); break;
+    case FAM_DIAG:
+      k_fw_denom<double, FAM_DIAG><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y, resid, tau2);
+      break;
+    case FAM_EDGE:
+      k_fw_denom<double, FAM_EDGE><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y, resid, tau2);
+      break;
+    default:
+      k_fw_denom<double, FAM_EDGE_C><<<grid, kBlock, 0, c->stream>>>(a, c->P.b, y, resid, tau2);
+      break;
   }
-#undef HL_FWD
+  HL_CHECK_LAUNCH(c);
+}
+
+void launch_resid64(Ctx* c, const void* U, int ld, int r, double* r64, int slot) {
+  OpArgs a = make_args(c, ld, slot);
+  const int grid = grid_for(c, c->P.n, kBlock);
+  HL_BY_FAM_TYPE(c, {
+    k_resid64<T, FAM><<<grid, kBlock, 0, c->stream>>>(a, (const T*)U, r, c->P.b, r64);
+  });
   HL_CHECK_LAUNCH(c);
 }
 

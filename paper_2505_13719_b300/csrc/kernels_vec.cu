@@ -121,15 +121,6 @@ __global__ void __launch_bounds__(kBlock) k_dvec(int64_t len, OpDvec op, double*
   grid_reduce<1>(red, partials, counter, out);
 }
 
-// a = b + s * (double) t, t of the factor type (dual update, p' for Lanczos)
-template <class T>
-__global__ void k_axpy_t(int64_t len, double* __restrict__ a, const double* __restrict__ b,
-                         const T* __restrict__ t, double s) {
-  for (int64_t i = (int64_t)blockIdx.x * kBlock + threadIdx.x; i < len;
-       i += (int64_t)gridDim.x * kBlock)
-    a[i] = b[i] + s * (double)t[i];
-}
-
 // out = (To) in, elementwise
 template <class To, class Ti>
 __global__ void k_convert(int64_t len, To* __restrict__ out, const Ti* __restrict__ in) {
@@ -235,12 +226,6 @@ void launch_trace_fix(Ctx* c, void* r, const void* src, const double* dscal, dou
   const int64_t m = c->P.m;
   HL_BY_TYPE(c, k_trace_fix<T><<<1, 32, 0, c->stream>>>(
                     (T*)r + (m - 1), src ? (const T*)src + (m - 1) : nullptr, dscal, add));
-  HL_CHECK_LAUNCH(c);
-}
-
-void launch_axpy_t(Ctx* c, int64_t len, double* a, const double* b, const void* t, double s) {
-  const int grid = grid_for(c, len, kBlock * 4);
-  HL_BY_TYPE(c, k_axpy_t<T><<<grid, kBlock, 0, c->stream>>>(len, a, b, (const T*)t, s));
   HL_CHECK_LAUNCH(c);
 }
 

@@ -347,7 +347,17 @@ __global__ void __launch_bounds__(kBlock) k_loop_x(int64_t nvec, const LoopCtl* 
   constexpr int VEC = V16<T>::N;
   const T* y = static_cast<const T*>(s.y);
   const T* xs = static_cast<const T*>(s.x_src);
-  const T w0 = (T)s.w0, w1 = (T)s.w1;
+  // coefficients in the factor type, converted by one thread of the block
+  __shared__ T s_c[5];
+  if (threadIdx.x == 0) {
+    s_c[0] = (T)s.w0;
+    s_c[1] = (T)s.w1;
+    s_c[2] = (T)s.c0;
+    s_c[3] = (T)s.c1;
+    s_c[4] = (T)s.c2;
+  }
+  __syncthreads();
+  const T w0 = s_c[0], w1 = s_c[1];
   T* xt = static_cast<T*>(s.xt);
   if (s.mode == 0) {
     for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < nvec;
@@ -362,7 +372,7 @@ __global__ void __launch_bounds__(kBlock) k_loop_x(int64_t nvec, const LoopCtl* 
   } else {
     const T* xts = static_cast<const T*>(s.xt_src);
     T* x = static_cast<T*>(s.x);
-    const T c0 = (T)s.c0, c1 = (T)s.c1, c2 = (T)s.c2;
+    const T c0 = s_c[2], c1 = s_c[3], c2 = s_c[4];
     for (int64_t v = (int64_t)blockIdx.x * kBlock + threadIdx.x; v < nvec;
          v += (int64_t)gridDim.x * kBlock) {
       T a[VEC], b[VEC], t[VEC], o[VEC], q[VEC];

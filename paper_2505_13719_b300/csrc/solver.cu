@@ -124,6 +124,7 @@ struct Solver {
   // the factor type that the operator kernels read (p itself in FP64);
   // residual vectors have the factor type: rpool[ir] holds A(YY^T) - b at Y
   double *p = nullptr, *pshift = nullptr;
+  double* r64 = nullptr;  // A(YY^T) - b in double at the HLR factor
   void* pk = nullptr;
   void* rpool[2] = {nullptr, nullptr};
   void* rX = nullptr;
@@ -141,7 +142,6 @@ struct Solver {
   ~Solver() { graph.release(); }
 
   void* Y() const { return pool[ic]; }
-  void* rY() const { return rpool[ir]; }
   double tau() const { return std::sqrt(P.tau2); }
   // unit roundoff of the stored factor: rounding the iterates moves g by up
   // to about u * mag; the acceptance tests of ADAP-FISTA step 2 and
@@ -173,6 +173,7 @@ struct Solver {
     for (auto& b : rpool) b = salloc<unsigned char>(m * elem_size(c));
     rX = salloc<unsigned char>(m * elem_size(c));
     pshift = salloc<double>(m);
+    r64 = salloc<double>(m);
     v = salloc<double>(n);
     vprev = salloc<double>(n);
     v0 = salloc<double>(n);
@@ -420,6 +421,28 @@ struct Solver {
                    lam, Mbar, H.Rn, rho, H.n_fista_iters, H.n_trials);
   }
 
+  // r64 = A(YY^T) - b at the HLR factor, every product in double from the
+  // stored factor (the trace row from |Y|_F^2); gs->rr and gs->nrm2 are
+  // replaced by the double values.  The dual update, the Lanczos shift, the
+  // Frank-Wolfe step and the KKT residual read these (in the mixed form the
+  // operator kernels' float residuals would carry rounding that beta
+  // amplifies into the multipliers).
+  void resid64(GradScal* gs) {
+    launch_resid64(c, Y(), ld, rank, r64, S_VEC2 + 10);
+    fetch();
+    double rr = c->h_scal[S_VEC2 + 10];
+    const double nrm2 = c->h_scal[S_VEC2 + 11];
+    if (P.has_trace) {
+      const double rt = nrm2 - b_tr;
+      rr += rt * rt;
+      c->h_scal[S_SCALE + 5] = rt;
+      HL_CUDA(cudaMemcpyAsync(r64 + (m - 1), c->h_scal + S_SCALE + 5, sizeof(double),
+                              cudaMemcpyHostToDevice, c->stream));
+    }
+    gs->rr = rr;
+    gs->nrm2 = nrm2;
+  }
+
   // the pool index other than ic and `busy` (the destination of a new factor)
   int free_slot() const { return (ic + 1) % 3; }
 
@@ -478,7 +501,8 @@ struct Solver {
         R.hlr_iters++;
         double GdotX = 0.0;                                         // G . YY^T = <GY, Y>
         aipp(rho_t, &gs, &GdotX);                                   // step 6
-        launch_axpy_t(c, m, pshift, p, rY(), beta);                 // p' = p + beta r(Y)
+        resid64(&gs);                                               // r(Y) in double
+        launch_dvec(c, 0, m, pshift, p, r64, beta, -1);             // p' = p + beta r(Y)
         const uint64_t sd = o.seed + 7919ull * (uint64_t)R.hlr_iters;
         launch_splitmix(c, sd, v0, 0.1 / std::sqrt((double)n), have_vprev ? vprev : nullptr);
         const double eig_tol = o.lanczos_tol_rel * eps_t / P.tau2;  // step 7
@@ -492,7 +516,7 @@ struct Solver {
         if (gap <= eps_t) break;                                    // step 8
         if (hl + 1 == o.max_hlr) break;                             // HLR limit: keep Y
         // Frank-Wolfe step (eqs. FW stepsize, tilde Y)              // step 11
-        launch_fw_denom(c, v, rY(), theta > 0.0 ? P.tau2 : 0.0, S_VEC2);
+        launch_fw_denom(c, v, r64, theta > 0.0 ? P.tau2 : 0.0, S_VEC2);
         fetch();
         double ssq = c->h_scal[S_VEC2];
         if (P.has_trace) {
@@ -527,8 +551,8 @@ struct Solver {
         if (rank > o.r_cap) trim_rank();
         check_time();
       }
-      // U_t = Y; dual update p_t = p + beta r (step 14)
-      launch_axpy_t(c, m, p, p, rY(), beta);
+      // U_t = Y; dual update p_t = p + beta r (step 14), r in double
+      launch_dvec(c, 0, m, p, p, r64, beta, -1);
       refresh_pk();
       if (P.has_trace) p_tr += beta * (gs.nrm2 - b_tr);
       launch_dvec(c, 1, m, nullptr, P.b, p, 0.0, S_VEC2 + 4);
