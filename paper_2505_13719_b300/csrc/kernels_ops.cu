@@ -292,13 +292,17 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AI
 #pragma unroll
         for (int v = 0; v < VEC; ++v) cdot_l = tfma(u[k][v], acc[k][v], cdot_l);
     }
-    acc_t0.add(cdot_l);
-    acc_mag.add(tabs(cdot_l));
     if (lane_g == 0) {
-      acc_t0.add(cdi * nrm);
-      acc_mag.add(tabs(cdi) * nrm);
+      acc_t0.add(cdot_l + cdi * nrm);
+      acc_mag.add(tabs(cdot_l) + tabs(cdi) * nrm);
+    } else {
+      acc_t0.add(cdot_l);
+      acc_mag.add(tabs(cdot_l));
     }
 
+    // the epilogue's sums of this row, added to the compensated
+    // accumulators once per row
+    T rs0 = (T)0, rs1 = (T)0, rs2 = (T)0, rs3 = (T)0;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int ch = lane_g + k * G;
@@ -316,38 +320,35 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AI
       } else if constexpr (EPI == EPI_FISTA_Z) {
         T cc[VEC], zz[VEC];
         load_chunk<T>(ctr, rowoff + ch * VEC, cc);
-        T sz = (T)0, sgx = (T)0, sgg = (T)0;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const T g = tfma(c2lam, w[v], u[k][v] - cc[v]);
           zz[v] = tfma(-invL, g, u[k][v]);
-          sz = tfma(zz[v], zz[v], sz);
-          sgx = tfma(g, u[k][v], sgx);
-          sgg = tfma(g, g, sgg);
+          rs0 = tfma(zz[v], zz[v], rs0);
+          rs1 = tfma(g, u[k][v], rs1);
+          rs2 = tfma(g, g, rs2);
         }
         store_chunk<T>(W, rowoff + ch * VEC, zz);
-        e0s.add(sz);
-        e1s.add(sgx);
-        e2s.add(sgg);
       } else {
         T cc[VEC], zz[VEC];
         load_chunk<T>(ctr, rowoff + ch * VEC, cc);
         load_chunk<T>(zin, rowoff + ch * VEC, zz);
-        T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const T D = u[k][v] - cc[v];
           const T VmD = tfma(c2lam, w[v], Lt * (zz[v] - u[k][v]));
-          s0 = tfma(VmD + D, D, s0);
-          s1 = tfma(D, D, s1);
-          s2 = tfma(VmD, VmD, s2);
-          s3 = tfma(w[v], u[k][v], s3);
+          rs0 = tfma(VmD + D, D, rs0);
+          rs1 = tfma(D, D, rs1);
+          rs2 = tfma(VmD, VmD, rs2);
+          rs3 = tfma(w[v], u[k][v], rs3);
         }
-        e0s.add(s0);
-        e1s.add(s1);
-        e2s.add(s2);
-        e3s.add(s3);
       }
+    }
+    if constexpr (EPI != EPI_W) {
+      e0s.add(rs0);
+      e1s.add(rs1);
+      e2s.add(rs2);
+      if constexpr (EPI == EPI_AIPP) e3s.add(rs3);
     }
   }
   if constexpr (EPI == EPI_W) {
@@ -416,6 +417,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
   for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
     T x[K][VEC], d[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
+    T rs0 = (T)0, rs1 = (T)0, rs2 = (T)0;  // YZ: this row's prox sums
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int ch = lane_g + k * G;
@@ -429,18 +431,14 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
           T cc[VEC];
           load_chunk<T>(ctr, rowoff + ch * VEC, cc);
           store_chunk<T>(yout, rowoff + ch * VEC, y);
-          T s0 = (T)0, s1 = (T)0, s2 = (T)0;
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
             const T dd = y[v] - x[k][v];
             const T yc = y[v] - cc[v];
-            s0 = tfma(dd, dd, s0);
-            s1 = tfma(dd, (T)0.5 * (y[v] + x[k][v]) - cc[v], s1);
-            s2 = tfma(yc, yc, s2);
+            rs0 = tfma(dd, dd, rs0);
+            rs1 = tfma(dd, (T)0.5 * (y[v] + x[k][v]) - cc[v], rs1);
+            rs2 = tfma(yc, yc, rs2);
           }
-          e0s.add(s0);
-          e1s.add(s1);
-          e2s.add(s2);
         }
       } else {
 #pragma unroll
@@ -455,8 +453,12 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
     for (int k = 0; k < K; ++k)
 #pragma unroll
       for (int v = 0; v < VEC; ++v) own_l = tfma(d[k][v], d[k][v] + (T)2 * x[k][v], own_l);
+    if constexpr (YZ) {
+      e0s.add(rs0);
+      e1s.add(rs1);
+      e2s.add(rs2);
+    }
     acc_tr.add(own_l);               // trace row change (lane parts)
-    acc_t0.add(cdiag[i] * own_l);    // diagonal of C
     if (Tr::kDiag) {
       const T dt = group_sum<G>(own_l, gmask);
       if (lane_g == 0) {
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
         }
       }
     }
-    acc_t0.add(cd_l);
+    acc_t0.add(cd_l + cdiag[i] * own_l);  // sparse C part and the diagonal of C
   }
   if constexpr (YZ) {
     Acc<T> red[7] = {acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s};
