@@ -98,6 +98,8 @@ def run_kernel(args):
     W = torch.empty_like(U)
     p = torch.randn(inst.m, device="cuda", dtype=torch.float64, generator=gen)
     res = torch.empty(inst.m, device="cuda", dtype=torch.float64)
+    if args.kernel == "gram":
+        return run_gram(args, H, hd, inst, prec, tdt, stream)
     if args.kernel == "grad":
         cls, name = 0, "fused_constraint_map_shift_spmm"
         call = lambda: H.hallar_grad(hd.h, U, r, p, 1.5, W, res)  # noqa: E731
@@ -123,6 +125,41 @@ def run_kernel(args):
             "bytes_per_launch": by[cls] / nl[cls],
             "bytes_with_padding_per_launch": bp[cls] / nl[cls], "achieved_GBps": round(gbs, 1),
             "peak_GBps": peaks["hbm_gbs"], "frac": round(gbs / peaks["hbm_gbs"], 4)}
+
+
+def run_gram(args, H, hd, inst, prec, tdt, stream):
+    """The rank trim (hallar_trim_rank: Gram Y^T Y, its eigenvectors, Y Q_k)
+    of an n x (r_cap + 1) factor; in the mixed form the Gram runs on the
+    tcgen05 tensor cores.  Reports the trim's time per call (CUDA events)
+    and the Gram's arithmetic rate on 2 n r^2 flops."""
+    import torch
+
+    r = args.rank
+    k = r - 1
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    Y = torch.randn(inst.n, r, device="cuda", dtype=torch.float64, generator=gen).to(tdt)
+    out = torch.empty(inst.n, k, device="cuda", dtype=tdt)
+    eigs = np.empty(r)
+    for _ in range(args.warmup):
+        H.hallar_trim_rank(hd.h, Y, r, k, out, eigs)
+    ts = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.hallar_trim_rank(hd.h, Y, r, k, out, eigs)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    hd.close()
+    t = statistics.median(ts)
+    flops = 2.0 * inst.n * r * r
+    return {"kernel": "rank_trim_gram", "workload": WORKLOADS[args.workload]["desc"],
+            "precision": args.precision, "rank": r, "kept": k, "calls": len(ts),
+            "trim_ms": round(1e3 * t, 3), "gram_flops": flops,
+            "note": "trim = Gram + host eigendecomposition + Y Q_k; the rate below counts "
+                    "the Gram's 2 n r^2 flops over the whole trim",
+            "trim_gflops": round(flops / t / 1e9, 1)}
 
 
 # ---------------------------------------------------------------------------
@@ -869,7 +906,7 @@ def main():
                          "from CUDA graphs: for profilers")
     ap.add_argument("--no-tol2", action="store_true",
                     help="skip the extra solve at KKT 5e-6 (objective check)")
-    ap.add_argument("--kernel", choices=["grad", "change"], default=None,
+    ap.add_argument("--kernel", choices=["grad", "change", "gram"], default=None,
                     help="time one operator kernel alone instead of full solves")
     ap.add_argument("--rank", type=int, default=10, help="factor width for --kernel")
     ap.add_argument("--serve", action="store_true",

@@ -96,7 +96,7 @@ constexpr int kGradRed = EPI == EPI_W ? 4 : (EPI == EPI_FISTA_Z ? 7 : 8);
 // CJ: C has the implicit C_J 11^T part (a compile-time switch: an unused
 // runtime branch would still cost predicated instructions in the row loop)
 template <class T, int FAM, int G, int K, bool CJ, int EPI>
-__global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AIPP ? 3 : 4>) k_grad(OpArgs a, GradIO io, GradInd gi,
+__global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_W ? 4 : 3>) k_grad(OpArgs a, GradIO io, GradInd gi,
                                                  const GradInd* __restrict__ gind) {
   using Tr = FamTraits<FAM>;
   constexpr int VEC = V16<T>::N;
@@ -142,7 +142,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AI
   // sum |p'_l| |A_l.UU^T| + |C terms| that scales the rounding of g;
   // e0..e3: the epilogue's sums
   Acc<T> acc_t0, acc_pr, acc_rr, acc_mag, e0s, e1s, e2s, e3s;
-  for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
+  // the next row's entry range is loaded one iteration ahead, so a row's
+  // column loads need not wait for its row pointers
+  int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G;
+  int e0n = 0, e1n = 0;
+  if (i < a.n) {
+    e0n = a.rowptr[i];
+    e1n = a.rowptr[i + 1];
+  }
+  for (; i < a.n; i += ngroups) {
+    const int e0 = e0n, e1 = e1n;
+    if (i + ngroups < a.n) {
+      e0n = a.rowptr[i + ngroups];
+      e1n = a.rowptr[i + ngroups + 1];
+    }
     T u[K][VEC], acc[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
 #pragma unroll
@@ -182,7 +195,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_AI
     }
     if (Tr::kPairs) dcoef += ps_tr;
 
-    const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
     T cdot_l = (T)0;  // lane part of <U_i, sum_j C_ij U_j> over the C entries
     // one merged entry (column j, C value cv, constraint code cd) with the
     // gathered row U_j
@@ -381,7 +393,7 @@ template <bool YZ>
 constexpr int kDiffRed = YZ ? 7 : 4;
 
 template <class T, int FAM, int G, int K, bool YZ>
-__global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) k_value_change(OpArgs a, DiffIO io, VcInd vi,
+__global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_change(OpArgs a, DiffIO io, VcInd vi,
                                                          const VcInd* __restrict__ vind) {
   using Tr = FamTraits<FAM>;
   constexpr int VEC = V16<T>::N;
@@ -414,7 +426,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
   // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT; YZ:
   // |D|^2, <D, (Y + X)/2 - centre>, |Y - centre|^2
   Acc<T> acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s;
-  for (int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G; i < a.n; i += ngroups) {
+  // the next row's entry range is loaded one iteration ahead, so a row's
+  // column loads need not wait for its row pointers
+  int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G;
+  int e0n = 0, e1n = 0;
+  if (i < a.n) {
+    e0n = a.rowptr[i];
+    e1n = a.rowptr[i + 1];
+  }
+  for (; i < a.n; i += ngroups) {
+    const int e0 = e0n, e1 = e1n;
+    if (i + ngroups < a.n) {
+      e0n = a.rowptr[i + ngroups];
+      e1n = a.rowptr[i + ngroups + 1];
+    }
     T x[K][VEC], d[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
     T rs0 = (T)0, rs1 = (T)0, rs2 = (T)0;  // YZ: this row's prox sums
@@ -468,7 +493,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, YZ ? 3 : 4>) 
         if (rYv) rYv[i] = rx + dt;
       }
     }
-    const int e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
     T cd_l = (T)0;
     // gathered rows X_j and Y_j (Y_j = cs Z_j in the YZ form)
     auto gather = [&](int64_t j, T (&xj)[K][VEC], T (&yj)[K][VEC]) {
