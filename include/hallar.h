@@ -96,7 +96,8 @@ typedef struct {
   double chi;             /* ADAP-FISTA parameter chi in (0,1) (0.5)              */
   double lambda0;         /* initial ADAP-AIPP prox stepsize (1)                  */
   double beta0;           /* initial penalty beta_1 (1)                           */
-  double beta_max;        /* cap of the penalty schedule (1e8)                    */
+  double beta_max;        /* cap of the penalty schedule, in units of
+                           * 1 + ||C||_1 (1e8)                                    */
   double eps_decay;       /* epsilon_{t+1} = eps_decay * epsilon_t (0.5)          */
   double eps1_rel;        /* epsilon_1 = eps1_rel (1 + tau^2 ||C||_1) (1e-2)      */
   double lanczos_tol_rel; /* Ritz residual tol = this * epsilon_t / tau^2 (0.5)   */
@@ -109,6 +110,13 @@ typedef struct {
   int32_t lanczos_kmax;   /* Lanczos basis size before a restart (300)            */
   int32_t precision;      /* hallar_precision                                     */
   int32_t verbose;        /* 1: one line per AL iteration on stderr               */
+  int32_t promote;        /* HALLAR_MIXED only (1): when ADAP-AIPP's prox steps no
+                           * longer move the float factor (four ADAP-AIPP calls of
+                           * one AL iteration end on a step that left W
+                           * unchanged), the solve continues in FP64 from its own
+                           * iterate (factor widened exactly; p, beta, lambda
+                           * carried over) and returns the solution as float.
+                           * 0: never                                           */
   uint64_t seed;          /* seed of the Lanczos start vectors (SplitMix64)       */
   void* stream;           /* cudaStream_t to issue on; NULL: the handle's own     */
 } hallar_options;
@@ -122,6 +130,8 @@ typedef struct {
   int32_t rank, converged;
   int32_t outer_iters, hlr_iters, aipp_iters, fista_iters, fista_failures;
   int32_t lanczos_iters, fw_steps, trims;
+  int32_t promoted_at;    /* AL iteration after which a mixed solve went on in
+                           * FP64 (options.promote), 0 if it did not */
   int64_t grad_evals, value_evals, kernel_launches;
 } hallar_result;
 
@@ -365,7 +375,9 @@ typedef struct {
 
 /* Estimated device bytes of one solve of req (problem data, the solver's
  * factors and vectors, the Lanczos basis, staging and reduction buffers, plus
- * 5 % and 64 MB of allocator slack); host arithmetic only.  -1 if req is NULL. */
+ * 5 % and 64 MB of allocator slack; a mixed request with opt.promote counts
+ * its factor buffers at 8 bytes an entry, what they hold after a promotion);
+ * host arithmetic only.  -1 if req is NULL. */
 int64_t hallar_solve_footprint(const hallar_request* req);
 
 /* Start a server (worker threads; no device memory until requests run).

@@ -634,9 +634,13 @@ def hallar_solve(inst, U0, p0=None, opt: Options | None = None, log=None):
       the nonconvex solver gets rho_t = epsilon_t / tau so that
       <R, Y> <= epsilon_t on the ball (Alg. 1 step 6 passes epsilon_t).
     * beta_t: start at beta0; after each dual update, double beta (capped at
-      beta_max) when ||r_t|| > ||r_{t-1}|| / 4 while the relative primal
-      infeasibility is still above tol (a LANCELOT-style test: the penalty
-      grows only while infeasibility is the obstacle).
+      beta_max (1 + ||C||_1)) when ||r_t|| > ||r_{t-1}|| / 4 while the
+      relative primal infeasibility is still above tol (a LANCELOT-style
+      test: the penalty grows only while infeasibility is the obstacle).
+      The cap is in units of 1 + ||C||_1: scaling C by s leaves the AL
+      iterates unchanged when beta and p scale by s too, so an absolute cap
+      would stop the theta SDP (||C||_1 = n) before its multipliers reach
+      their optimal size, which grows like n / degree.
     * termination: eq. termination2 at relative tolerance tol.
     * U0 outside the ball is projected onto it.
     """
@@ -702,7 +706,7 @@ def hallar_solve(inst, U0, p0=None, opt: Options | None = None, log=None):
             break
         rnorm = float(np.linalg.norm(r))
         if rp > opt.tol and rnorm > 0.25 * prev_rnorm:
-            beta = min(2.0 * beta, opt.beta_max)
+            beta = min(2.0 * beta, opt.beta_max * (1.0 + cnorm))
         prev_rnorm = rnorm
         if time.perf_counter() - t0 > opt.time_limit_s:
             break

@@ -462,6 +462,7 @@ hallar_status hallar_default_options(hallar_options* o) {
   o->lanczos_kmax = 300;
   o->precision = HALLAR_FP64;
   o->verbose = 0;
+  o->promote = 1;
   o->seed = 0;
   o->stream = nullptr;
   return HALLAR_OK;
@@ -491,7 +492,8 @@ hallar_status hallar_create(int64_t n, int64_t n1, const int64_t* C_rowptr, cons
         !(o.lambda0 > 0.0) || !(o.beta0 > 0.0) || !(o.beta_max >= o.beta0) ||
         !(o.eps_decay > 0.0 && o.eps_decay <= 1.0) || !(o.eps1_rel > 0.0) ||
         !(o.lanczos_tol_rel > 0.0) || !(o.time_limit_s > 0.0) || o.max_fista < 1 ||
-        o.max_aipp < 1 || o.max_outer < 1 || o.max_hlr < 1 || o.lanczos_kmax < 2)
+        o.max_aipp < 1 || o.max_outer < 1 || o.max_hlr < 1 || o.lanczos_kmax < 2 ||
+        (o.promote != 0 && o.promote != 1))
       fail(HALLAR_EINVAL, "invalid options");
     HL_CUDA(cudaGetDevice(&c->device));
     HL_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));

@@ -149,6 +149,7 @@ struct LoopCtl {
   double A, tk, L, Ln, a, Lacc;
   int fista_it, fista_status, trials, aipp_j;
   int done, attempts, error, graph_mode;
+  int stall_exit;              // done on a prox step that left W unchanged
   // operator scalars at the accepted W (valid when done)
   double gT0, gpr, grr, gmag, gnrm2, gWU, Rn;
   // counters since the call started

@@ -327,6 +327,7 @@ __global__ void k_aipp_ctl(LoopCtl* Lp, const double* __restrict__ h) {
       L.n_aipp_iters++;
       // step 3; a prox step that left W unchanged cannot make progress
       if (L.Rn <= L.rho || stalled || L.aipp_j >= L.max_aipp) L.done = 1;
+      L.stall_exit = stalled;
     } else {
       L.lam /= 2.0;
       if (L.lam < 1e-30) L.error = HALLAR_ENUMERIC;

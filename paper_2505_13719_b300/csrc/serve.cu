@@ -187,7 +187,9 @@ int64_t hallar_solve_footprint(const hallar_request* q) {
   // solver: ten factor-sized buffers, vectors of length m and n, Gram matrix
   const int64_t rcap = std::max(q->opt.r_cap, 1);
   const int64_t ld = padded(rcap + 1, mixed ? 4 : 2);
-  b += 10 * n * ld * es + m * (8 + 4 + 3 * es + 8) + 24 * n + ld * ld * 8;
+  // a mixed solve that goes on in FP64 (opt.promote) holds 8-byte factors then
+  const int64_t esf = mixed && q->opt.promote ? 8 : es;
+  b += 10 * n * ld * esf + m * (8 + 4 + 3 * esf + 8) + 24 * n + ld * ld * 8;
   // Lanczos: row-major basis, two vectors, per-block partial rows
   int64_t k = std::min<int64_t>(std::min<int64_t>(std::max(q->opt.lanczos_kmax, 2), 512), n);
   const int64_t kcap = padded(k, 4);

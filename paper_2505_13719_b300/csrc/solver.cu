@@ -13,8 +13,8 @@
 // as the oracle's:
 //   * epsilon_t = max(tol/2 (1 + |pval|), eps_1 eps_decay^(t-1)),
 //     eps_1 = eps1_rel (1 + tau^2 ||C||_1); ADAP-AIPP gets rho = epsilon_t / tau;
-//   * beta doubles (<= beta_max) when ||r_t|| > ||r_{t-1}|| / 4 while the
-//     relative primal infeasibility is above tol;
+//   * beta doubles (<= beta_max (1 + ||C||_1)) when ||r_t|| > ||r_{t-1}|| / 4
+//     while the relative primal infeasibility is above tol;
 //   * ADAP-AIPP: M_j = max(1, Mbar_{j-1}/2), lambda carried across calls;
 //   * ADAP-FISTA: linearisation test with g(y) - g(x~) formed as a
 //     difference; V = grad psi(y) - grad psi(x~) + L (x~ - y);
@@ -28,6 +28,8 @@
 //   * theta = 0: no zero column is appended; rank above r_cap: keep the
 //     r_cap leading directions of YY^T (Gram eigenvectors);
 //   * termination: eq. termination2, ||C||_1 the induced norm.
+// Not in the oracle: a mixed solve whose float factor stalls goes on in FP64
+// (options.promote).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -135,10 +137,12 @@ struct Solver {
   LoopGraph graph;
   int rank = 0, ld = 0;
   double beta = 1.0, lam = 1.0, Mbar = 1.0, p_tr = 0.0, b_tr = 0.0;
+  int prec0 = HALLAR_FP64;  // the handle's form (a promoted solve returns to it)
+  int stalls_t = 0;         // ADAP-AIPP calls of this AL iteration that stalled
   hallar_result R{};
   std::chrono::steady_clock::time_point t0;
 
-  explicit Solver(Ctx* cc) : c(cc), P(cc->P), o(cc->opt) {}
+  explicit Solver(Ctx* cc) : c(cc), P(cc->P), o(cc->opt), prec0(cc->opt.precision) {}
   ~Solver() { graph.release(); }
 
   void* Y() const { return pool[ic]; }
@@ -397,6 +401,7 @@ struct Solver {
       }
       c->launches += graph.k_outer * H.n_attempts + graph.k_trial * H.n_trials;
     }
+    if (H.stall_exit) stalls_t++;
     R.fista_iters += (int32_t)H.n_fista_iters;
     R.fista_failures += (int32_t)H.n_fista_fail;
     R.aipp_iters += (int32_t)H.n_aipp_iters;
@@ -458,6 +463,71 @@ struct Solver {
     R.trims++;
   }
 
+  // ---- promotion of a mixed solve to FP64 ---------------------------------
+  // A float factor resolves each entry to 2^-24 of its size.  Once beta has
+  // grown so far that ADAP-AIPP's prox steps round away (W unchanged while
+  // |R| > rho), neither ADAP-AIPP nor the Frank-Wolfe update (sqrt(1 - alpha)
+  // rounds to 1) can move the iterate, and the residual stops falling.  (A
+  // step that leaves W bitwise unchanged also gives V = 0, so such a call
+  // reports |R| = 0: the sign is the repeated stall, whatever |R| is.)  The
+  // solve then goes on in FP64 from where it is: the factor is widened (exact),
+  // p, beta, lambda and Mbar carry over, and every kernel from here on is the
+  // FP64 instantiation.  The float ld (a multiple of 4) is a valid FP64 ld.
+  static constexpr int kPromoteStalls = 4;
+
+  void release_buf(void*& q) {
+    auto it = std::find(mine.begin(), mine.end(), q);
+    if (it != mine.end()) mine.erase(it);
+    dfree(c, q);
+    q = nullptr;
+  }
+
+  void promote(int t) {
+    const size_t fb64 = (size_t)n * ld_max * sizeof(double);
+    double* y64 = salloc<double>((size_t)n * ld_max);
+    launch_to_double(c, n * (int64_t)ld, y64, Y());  // before the form changes
+    for (auto& b : pool) release_buf(b);
+    release_buf(xb);
+    release_buf(xtb);
+    release_buf(zb);
+    for (auto& b : rpool) release_buf(b);
+    release_buf(rX);
+    if (pk != (void*)p) release_buf(pk);
+    c->opt.precision = HALLAR_FP64;  // o is the handle's options: unit(), H.mixed follow
+    fbytes = fb64;
+    pool[0] = y64;
+    pool[1] = fbuf();
+    pool[2] = fbuf();
+    xb = fbuf();
+    xtb = fbuf();
+    zb = fbuf();
+    for (auto& b : rpool) b = salloc<double>(m);
+    rX = salloc<double>(m);
+    pk = p;
+    ic = 0;
+    ir = 0;
+    graph.release();  // the captured kernels are the float instantiations
+    R.promoted_at = t;
+    if (o.verbose)
+      std::fprintf(stderr, "[hallar] t=%d mixed form stalled (%d ADAP-AIPP calls): FP64 from here\n",
+                   t, stalls_t);
+  }
+
+  // after a promoted solve: the handle's form again, and the factor in it
+  // for hallar_get_solution
+  void narrow_solution() {
+    if (!R.promoted_at || o.precision == prec0) {
+      c->opt.precision = prec0;
+      return;
+    }
+    void* y32 = salloc<float>((size_t)n * ld);
+    const void* y64 = Y();
+    c->opt.precision = prec0;
+    launch_to_factor_type(c, n * (int64_t)ld, y32, (const double*)y64);
+    pool[ic] = y32;
+    graph.release();
+  }
+
   hallar_status run(const void* U0d, int r0, const double* p0d, hallar_result* out) {
     t0 = std::chrono::steady_clock::now();
     const double tauv = tau();
@@ -484,6 +554,7 @@ struct Solver {
     lam = o.lambda0;
     Mbar = 1.0;
     const double eps1 = o.eps1_rel * (1.0 + P.tau2 * P.c_norm1);
+    const double beta_cap = o.beta_max * (1.0 + P.c_norm1);  // in units of 1 + |C|_1
     double prev_rnorm = INFINITY;
     bool have_vprev = false;
     grad_enqueue(Y(), nullptr, nullptr);  // pval at the start point
@@ -494,6 +565,7 @@ struct Solver {
     hallar_status st = HALLAR_ENOTCONV;
     for (int t = 1; t <= o.max_outer; ++t) {
       R.outer_iters++;
+      stalls_t = 0;
       const double eps_floor = 0.5 * o.tol * (1.0 + std::fabs(pval_now));
       const double eps_t = std::fmax(eps_floor, eps1 * std::pow(o.eps_decay, t - 1));
       const double rho_t = eps_t / std::fmax(tauv, 1e-300);
@@ -587,12 +659,14 @@ struct Solver {
         R.converged = 1;
         break;
       }
+      if (o.promote && o.precision == HALLAR_MIXED && stalls_t >= kPromoteStalls) promote(t);
       // the penalty grows only while primal infeasibility is above the tolerance
-      if (rp > o.tol && rnorm > 0.25 * prev_rnorm) beta = std::fmin(2.0 * beta, o.beta_max);
+      if (rp > o.tol && rnorm > 0.25 * prev_rnorm) beta = std::fmin(2.0 * beta, beta_cap);
       prev_rnorm = rnorm;
       pval_now = pval;
       check_time();
     }
+    narrow_solution();
     sync(c);
     R.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     c->sol_U = Y();
@@ -651,6 +725,13 @@ hallar_status solve(Ctx* c, const void* U0, int r0, const double* p0, hallar_res
     if (res) res->kernel_launches = c->launches - launches0;
     return st;
   } catch (const Err& e) {
+    // a promoted solve leaves the handle in its own form, with a solution in it
+    try {
+      s.narrow_solution();
+    } catch (const Err&) {
+      c->opt.precision = s.prec0;
+      s.pool[s.ic] = nullptr;
+    }
     keep_buffers();
     s.R.seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - s.t0).count();

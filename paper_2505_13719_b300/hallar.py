@@ -42,7 +42,7 @@ class hallar_options(C.Structure):
                 ("r_cap", C.c_int32), ("max_outer", C.c_int32), ("max_hlr", C.c_int32),
                 ("max_aipp", C.c_int32), ("max_fista", C.c_int32),
                 ("lanczos_kmax", C.c_int32), ("precision", C.c_int32),
-                ("verbose", C.c_int32), ("seed", C.c_uint64), ("stream", C.c_void_p)]
+                ("verbose", C.c_int32), ("promote", C.c_int32), ("seed", C.c_uint64), ("stream", C.c_void_p)]
 
 
 class hallar_result(C.Structure):
@@ -54,7 +54,7 @@ class hallar_result(C.Structure):
                 ("hlr_iters", C.c_int32), ("aipp_iters", C.c_int32),
                 ("fista_iters", C.c_int32), ("fista_failures", C.c_int32),
                 ("lanczos_iters", C.c_int32), ("fw_steps", C.c_int32), ("trims", C.c_int32),
-                ("grad_evals", C.c_int64), ("value_evals", C.c_int64),
+                ("promoted_at", C.c_int32), ("grad_evals", C.c_int64), ("value_evals", C.c_int64),
                 ("kernel_launches", C.c_int64)]
 
     def as_dict(self):

@@ -92,6 +92,8 @@ def test_closed_form(H, name, make, ref, prec):
     val = inst.sense * res.pval
     tol = OBJ_TOL_MIXED_THETA if (prec == 1 and inst.family == "edge") else OBJ_TOL[prec]
     assert abs(val - ref) <= tol * abs(ref), (val, ref)
+    if inst.family == "diag":
+        assert res.promoted_at == 0  # Max-Cut converges in the float form
     assert np.linalg.norm(U) <= math.sqrt(inst.tau2) * (1 + 1e-6)
 
 
@@ -135,21 +137,18 @@ STORED = {
 STORED_TIME_LIMIT = {"theta_gnm_n40_m80": 600.0}
 
 
-# The mixed form does not solve theta on the random graph G(40, 80): as the
-# penalty grows the ADAP-AIPP steps fall below the float factor's
-# resolution, the prox step stalls, the residual stops falling and the
-# LANCELOT-style rule doubles beta up to its cap (measured: beta 1e8, 300
-# outer iterations, relative gap 0.6; FP64 converges in 21).  The case is
-# kept, as an expected failure that turns into a failure if it passes.
-MIXED_STORED_XFAIL = {"theta_gnm_n40_m80"}
+# The float factor alone does not solve theta on the random graph G(40, 80):
+# as the penalty grows, ADAP-AIPP's prox steps fall below its resolution and
+# stall, and the residual stops falling (measured with promotion off: beta
+# 1e8, 300 outer iterations, relative gap 0.6; FP64 converges in 21).  With
+# options.promote (the default) the mixed solve sees the stalls and goes on
+# in FP64; the Max-Cut cases never stall.
+MIXED_PROMOTES = {"theta_gnm_n40_m80"}
 
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("name", sorted(STORED))
-def test_against_stored_oracle_solve(H, name, prec, request):
-    if prec == 1 and name in MIXED_STORED_XFAIL:
-        request.applymarker(pytest.mark.xfail(
-            strict=True, reason="mixed form: float factor resolution stalls theta on G(40, 80)"))
+def test_against_stored_oracle_solve(H, name, prec):
     stored = json.load(open(GOLDEN))
     assert name in stored, f"no stored oracle value for {name}: run tests/golden/make_golden.py"
     ref = stored[name]
@@ -160,6 +159,7 @@ def test_against_stored_oracle_solve(H, name, prec, request):
                               time_limit_s=STORED_TIME_LIMIT.get(name, 60.0))
     assert st == H.HALLAR_OK, res.as_dict()
     assert abs(res.pval - ref["pval"]) <= 1e-5 * abs(ref["pval"]), (res.pval, ref["pval"])
+    assert (res.promoted_at > 0) == (prec == 1 and name in MIXED_PROMOTES), res.as_dict()
 
 
 def test_solve_against_oracle_solve(H):

@@ -33,7 +33,11 @@ def test_footprint_grows_with_size_rank_and_precision(H):
     small, big = I.maxcut_torus(50, "unit"), I.maxcut_torus(100, "unit")
     assert footprint(H, big) > footprint(H, small)
     assert footprint(H, big, r_cap=64) > footprint(H, big, r_cap=8)
-    assert footprint(H, big, 0) > footprint(H, big, 1)  # float factors are half the size
+    # float factors are half the size, unless the solve may go on in FP64
+    assert footprint(H, big, 0) > footprint(H, big, 1, promote=0)
+    n, ld = big.n, 36  # r_cap 32 + 1 padded to 4 floats
+    assert footprint(H, big, 1, promote=1) - footprint(H, big, 1, promote=0) \
+        >= 10 * n * ld * 4
 
 
 def test_server_options_are_validated(H):
