@@ -109,7 +109,9 @@ typedef struct {
   int32_t max_fista;      /* ADAP-FISTA iterations per call (400)                 */
   int32_t lanczos_kmax;   /* Lanczos basis size before a restart (300)            */
   int32_t precision;      /* hallar_precision                                     */
-  int32_t verbose;        /* 1: one line per AL iteration on stderr               */
+  int32_t verbose;        /* 1: one line per AL iteration on stderr; 2: also one
+                           * per ADAP-AIPP call; 3: also ADAP-AIPP's step-2 test
+                           * (device printf, stdout)                            */
   int32_t promote;        /* HALLAR_MIXED only (1): when ADAP-AIPP's prox steps no
                            * longer move the float factor (four ADAP-AIPP calls of
                            * one AL iteration end on a step that left W

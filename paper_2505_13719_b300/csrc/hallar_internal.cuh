@@ -150,6 +150,7 @@ struct LoopCtl {
   int fista_it, fista_status, trials, aipp_j;
   int done, attempts, error, graph_mode;
   int stall_exit;              // done on a prox step that left W unchanged
+  int verbose;                 // >= 3: the control kernels print their step-2 tests
   // operator scalars at the accepted W (valid when done)
   double gT0, gpr, grr, gmag, gnrm2, gWU, Rn;
   // counters since the call started
@@ -168,7 +169,7 @@ struct LoopCtl {
 enum Slot : int {
   S_GRAD = 0,    // fused operator: C.UU^T part, p.r, r.r, magnitude, epilogue sums [4..7]
   S_PRE = 8,     // pre-pass: |U|_F^2, |colsum|^2
-  S_DIFF = 16,   // value change: dT0, p.dT, dT(2rX+dT), trace dT, [4..6] prox sums;
+  S_DIFF = 16,   // value change: dT0, p.dT, dT(2rX+dT), trace dT, [4..7] prox sums;
                  // [8..9] colsum-difference pass
   S_VEC = 32,    // streaming kernels
   S_VEC2 = 48,   // streaming kernels (second set)
@@ -327,8 +328,8 @@ inline void* cj_row(const Ctx* c) { return c->d_colsum + 3 * kColsumMax; }
 // p has the factor's element type (float copy in the mixed form)
 void launch_grad(Ctx* c, const void* U, int ld, int r, const void* p, double beta,
                  GradOut out);
-// the fused operator with the ADAP-FISTA (EPI_FISTA_Z: S_GRAD[4..6] = |z|^2,
-// <g, x~>, |g|^2) or ADAP-AIPP (EPI_AIPP: S_GRAD[4..7] = <V, D>, |D|^2,
+// the fused operator with the ADAP-FISTA (EPI_FISTA_Z: S_GRAD[4] = |z|^2) or
+// ADAP-AIPP (EPI_AIPP: S_GRAD[4..7] = <V, D>, |D|^2,
 // |V - D|^2, <W, y>) epilogue, its arguments read from device memory
 void launch_grad_epi(Ctx* c, int epi, int ld, int r, const void* p, const GradInd* gind);
 // g(Y) - g(X) pieces into S_DIFF: [0] dT0 (no C_J part) [1] p.dT [2] dT(2rX+dT)
@@ -336,8 +337,8 @@ void launch_grad_epi(Ctx* c, int epi, int ld, int r, const void* p, const GradIn
 void launch_value_change(Ctx* c, const void* X, const void* Y, int ld, int r,
                          const void* p, const void* rX, void* rY);
 // the same with arguments from device memory; y_from_z: Y = cs Z (cs from
-// S_GRAD[4] = |Z|^2 and tau), Y stored, and S_DIFF[4..6] = |Y - X|^2,
-// <Y - X, (Y + X)/2 - centre>, |Y - centre|^2
+// S_GRAD[4] = |Z|^2 and tau), Y stored, and S_DIFF[4..7] = |Y - X|^2,
+// <Y - X, (Y + X)/2 - centre>, |Y - centre|^2, <X - Z, Y - X>
 void launch_value_change_ind(Ctx* c, bool y_from_z, int ld, int r, const void* p,
                              const VcInd* vind);
 // colsum of D = Y - X and of Y + X (for the C_J part of a value change);

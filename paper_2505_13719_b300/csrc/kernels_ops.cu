@@ -82,8 +82,9 @@ struct GradIO {
 //   EPI_W        store W (hallar_grad, the outer loop)
 //   EPI_FISTA_Z  ADAP-FISTA step 2's unprojected step at U = x~ (Appendix A.1):
 //                g = grad psi_s(x~) = 2 lam W + x~ - centre, z = x~ - g / L;
-//                store z; reduce |z|^2, <g, x~>, |g|^2 (the ball projection
-//                y = min(1, tau/|z|) z and <g, y - x~> follow from these)
+//                store z; reduce |z|^2 (the ball projection's factor
+//                min(1, tau/|z|); the value change that forms y = P_B(z)
+//                reduces <g, y - x~>)
 //   EPI_AIPP     ADAP-AIPP step 2 at U = y (z its unprojected step):
 //                V - D = 2 lam W + L (z - y), D = y - centre; reduce <V, D>,
 //                |D|^2, |V - D|^2 (R_j = (V - D)/lam, eq. Rj def) and <W, y>
@@ -91,7 +92,7 @@ struct GradIO {
 // The pointers and coefficients come from a GradInd, by value or (when the
 // device-side ADAP-AIPP loop fills it) from device memory.
 template <int EPI>
-constexpr int kGradRed = EPI == EPI_W ? 4 : (EPI == EPI_FISTA_Z ? 7 : 8);
+constexpr int kGradRed = EPI == EPI_W ? 4 : (EPI == EPI_FISTA_Z ? 5 : 8);
 
 // CJ: C has the implicit C_J 11^T part (a compile-time switch: an unused
 // runtime branch would still cost predicated instructions in the row loop)
@@ -337,8 +338,6 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_W 
           const T g = tfma(c2lam, w[v], u[k][v] - cc[v]);
           zz[v] = tfma(-invL, g, u[k][v]);
           rs0 = tfma(zz[v], zz[v], rs0);
-          rs1 = tfma(g, u[k][v], rs1);
-          rs2 = tfma(g, g, rs2);
         }
         store_chunk<T>(W, rowoff + ch * VEC, zz);
       } else {
@@ -356,19 +355,19 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, EPI == EPI_W 
         }
       }
     }
-    if constexpr (EPI != EPI_W) {
-      e0s.add(rs0);
+    if constexpr (EPI != EPI_W) e0s.add(rs0);
+    if constexpr (EPI == EPI_AIPP) {
       e1s.add(rs1);
       e2s.add(rs2);
-      if constexpr (EPI == EPI_AIPP) e3s.add(rs3);
+      e3s.add(rs3);
     }
   }
   if constexpr (EPI == EPI_W) {
     Acc<T> red[4] = {acc_t0, acc_pr, acc_rr, acc_mag};
     grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);
   } else if constexpr (EPI == EPI_FISTA_Z) {
-    Acc<T> red[7] = {acc_t0, acc_pr, acc_rr, acc_mag, e0s, e1s, e2s};
-    grid_reduce_acc<T, 7>(red, a.partials, a.counter, a.out);
+    Acc<T> red[5] = {acc_t0, acc_pr, acc_rr, acc_mag, e0s};
+    grid_reduce_acc<T, 5>(red, a.partials, a.counter, a.out);
   } else {
     Acc<T> red[8] = {acc_t0, acc_pr, acc_rr, acc_mag, e0s, e1s, e2s, e3s};
     grid_reduce_acc<T, 8>(red, a.partials, a.counter, a.out);
@@ -390,7 +389,7 @@ struct DiffIO {
 };
 
 template <bool YZ>
-constexpr int kDiffRed = YZ ? 7 : 4;
+constexpr int kDiffRed = YZ ? 8 : 4;
 
 template <class T, int FAM, int G, int K, bool YZ>
 __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_change(OpArgs a, DiffIO io, VcInd vi,
@@ -424,8 +423,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_c
   const T cs = YZ ? s_cs : (T)1;
 
   // dT0 (sparse + diagonal part), p.dT, dT (2 rX + dT), trace dT; YZ:
-  // |D|^2, <D, (Y + X)/2 - centre>, |Y - centre|^2
-  Acc<T> acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s;
+  // |D|^2, <D, (Y + X)/2 - centre>, |Y - centre|^2 and <X - Z, D> (with
+  // Z = X - g/L this is <g, Y - X>/L, ADAP-FISTA step 2's linear term, taken
+  // from the vectors themselves: formed from <g, X> and |g|^2 it cancels
+  // catastrophically when the projection undoes a radial step)
+  Acc<T> acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s, e3s;
   // the next row's entry range is loaded one iteration ahead, so a row's
   // column loads need not wait for its row pointers
   int64_t i = ((int64_t)blockIdx.x * kBlock + threadIdx.x) / G;
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_c
     }
     T x[K][VEC], d[K][VEC];
     const int64_t rowoff = i * (int64_t)a.ld;
-    T rs0 = (T)0, rs1 = (T)0, rs2 = (T)0;  // YZ: this row's prox sums
+    T rs0 = (T)0, rs1 = (T)0, rs2 = (T)0, rs3 = (T)0;  // YZ: this row's prox sums
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int ch = lane_g + k * G;
@@ -451,19 +453,20 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_c
         load_chunk<T>(X, rowoff + ch * VEC, x[k]);
         load_chunk<T>(Yv, rowoff + ch * VEC, y);
         if constexpr (YZ) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) y[v] = cs * y[v];
           T cc[VEC];
           load_chunk<T>(ctr, rowoff + ch * VEC, cc);
-          store_chunk<T>(yout, rowoff + ch * VEC, y);
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
+            const T zv = y[v];
+            y[v] = cs * zv;
             const T dd = y[v] - x[k][v];
             const T yc = y[v] - cc[v];
             rs0 = tfma(dd, dd, rs0);
             rs1 = tfma(dd, (T)0.5 * (y[v] + x[k][v]) - cc[v], rs1);
             rs2 = tfma(yc, yc, rs2);
+            rs3 = tfma(x[k][v] - zv, dd, rs3);
           }
+          store_chunk<T>(yout, rowoff + ch * VEC, y);
         }
       } else {
 #pragma unroll
@@ -482,6 +485,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_c
       e0s.add(rs0);
       e1s.add(rs1);
       e2s.add(rs2);
+      e3s.add(rs3);
     }
     acc_tr.add(own_l);               // trace row change (lane parts)
     if (Tr::kDiag) {
@@ -593,8 +597,8 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks<T, FAM, G, K, 3>) k_value_c
     acc_t0.add(cd_l + cdiag[i] * own_l);  // sparse C part and the diagonal of C
   }
   if constexpr (YZ) {
-    Acc<T> red[7] = {acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s};
-    grid_reduce_acc<T, 7>(red, a.partials, a.counter, a.out);
+    Acc<T> red[8] = {acc_t0, acc_pd, acc_q, acc_tr, e0s, e1s, e2s, e3s};
+    grid_reduce_acc<T, 8>(red, a.partials, a.counter, a.out);
   } else {
     Acc<T> red[4] = {acc_t0, acc_pd, acc_q, acc_tr};
     grid_reduce_acc<T, 4>(red, a.partials, a.counter, a.out);

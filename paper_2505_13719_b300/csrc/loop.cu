@@ -17,6 +17,7 @@
 // g(y) - g(x) formed in difference form by the value-change kernel, and an
 // allowance of slack_u * lam * (sum of the magnitudes of g's terms).
 #include <cmath>
+#include <cstdio>
 
 #include "device_common.cuh"
 #include "hallar_internal.cuh"
@@ -183,12 +184,10 @@ __global__ void k_fista_ctl(LoopCtl* Lp, const double* __restrict__ h) {
   L.n_values++;
   if (L.error == 0 && L.fista_status == kFistaRunning) {
     const double nrm_xt2 = h[S_PRE];
-    const double zn = sqrt(h[S_GRAD + 4]);
-    const double cs = as_factor(L, zn > L.tau ? L.tau / zn : 1.0);
     const double invL = as_factor(L, 1.0 / L.Ln);
-    // <grad psi_s(x~), y - x~> with y = cs z, z = x~ - g invL:
-    // y - x~ = (cs - 1) x~ - cs invL g
-    const double gd = (cs - 1.0) * h[S_GRAD + 5] - cs * invL * h[S_GRAD + 6];
+    // <grad psi_s(x~), y - x~> = <x~ - z, y - x~> / invL (z = x~ - g invL),
+    // reduced from the vectors by the value change
+    const double gd = h[S_DIFF + 7] / invL;
     const double d2 = h[S_DIFF + 4], dlin = h[S_DIFF + 5], dy0 = h[S_DIFF + 6];
     const double dpsi = L.lam * change_value(L, h, nrm_xt2) + dlin;
     const double slack = L.slack_u * L.lam * magnitude(L, h, nrm_xt2);
@@ -202,11 +201,15 @@ __global__ void k_fista_ctl(LoopCtl* Lp, const double* __restrict__ h) {
       if (dy0 < L.chi * A_new * L.Ln * d2) {                       // step 4
         L.fista_status = kFistaFailure;
         L.n_fista_fail++;
+        if (L.verbose >= 3)
+          printf("[fista4] it=%d lam=%.6e dy0=%.9e A=%.9e Ln=%.9e d2=%.9e\n", L.fista_it,
+                 L.lam, dy0, A_new, L.Ln, d2);
       } else if (snorm <= L.sigma * sqrt(dy0)) {                   // step 5
         L.fista_status = kFistaSuccess;
       } else if (L.fista_it + 1 >= L.max_fista) {
         L.fista_status = kFistaFailure;
         L.n_fista_fail++;
+        if (L.verbose >= 3) printf("[fista-max] lam=%.6e\n", L.lam);
       } else {
         // step 3's x update and the next iteration's first x~ (whose
         // stepsize is the accepted Ln) in one pass after this kernel
@@ -301,6 +304,9 @@ __global__ void k_aipp_ctl(LoopCtl* Lp, const double* __restrict__ h) {
       const double slack = L.slack_u * L.lam * mag;
       stalled = D2 == 0.0;
       accept = stalled || -L.lam * dg - 0.5 * D2 >= -VD - slack;
+      if (L.verbose >= 3)
+        printf("[aipp2] j=%d lam=%.6e dg=%.9e D2=%.9e VD=%.9e slack=%.9e mag=%.9e %s\n",
+               L.aipp_j, L.lam, dg, D2, VD, slack, mag, accept ? "accept" : "reject");
       if (accept) {
         double T0 = h[S_GRAD] + L.C_J * h[S_PRE + 1];
         double pr = h[S_GRAD + 1], rr = h[S_GRAD + 2];

@@ -365,6 +365,7 @@ struct Solver {
     H.Mbar = Mbar;
     H.nrm_ctr2 = nrm_ctr2;
     H.graph_mode = eager ? 0 : 1;
+    H.verbose = o.verbose;
     if (!eager) {
       if (graph.ld != ld) build_graph();
       H.h_fista = graph.h_fista;
