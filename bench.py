@@ -741,6 +741,7 @@ KERNEL_SOURCES = ("paper_2505_13719_b300/csrc/kernels_ops.cu",
 TRAFFIC_PROFILES = {
     # (kernel class, precision, factor width) -> summary with the ncu figures
     ("fused_constraint_map_shift_spmm", "mixed", 10): "profiles/k_grad_torus1000_mixed_r10.md",
+    ("value_change", "mixed", 10): "profiles/k_value_change_torus1000_mixed_r10.md",
 }
 
 

@@ -238,3 +238,18 @@ def test_rank_trim_is_the_best_low_rank_approximation():
         Xk = Yk @ Yk.T
         assert np.linalg.norm(X - Xk) == pytest.approx(math.sqrt(np.sum(s[k:] ** 4)), rel=1e-10)
         assert np.linalg.eigvalsh(X - Xk)[0] >= -1e-10 * s[0] ** 2
+
+
+def test_penalty_cap_scales_with_the_cost_norm():
+    # Reading: beta_t doubles up to beta_max (1 + ||C||_1).  On theta(Q_6)
+    # (||C||_1 = n = 64) U ~ 1 stays a fixed point of the subproblem until
+    # the edge multipliers reach about n/d, so beta keeps doubling; with
+    # beta_max = 1 it must stop at exactly 1 + 64 = 65 and never pass it
+    inst = I.theta(64, *I.hypercube_graph(6))
+    assert O.c_norm1(inst) == 64.0
+    res = O.hallar_solve(inst, I.initial_factor(inst.n, 2, 7),
+                         opt=O.Options(tol=1e-7, beta_max=1.0, max_outer=14))
+    betas = [h["beta"] for h in res.history]
+    assert max(betas) == 65.0
+    assert betas[:8] == sorted(betas[:8])
+    assert all(b == 65.0 or b == 2.0 ** round(math.log2(b)) for b in betas)
