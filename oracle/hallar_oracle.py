@@ -435,6 +435,11 @@ def adap_fista(sub, lam, center, mu, L0, opt, tau):
     optimality gives L (x~ - y) - grad psi_s(x~) in N_B(y), so V lies in
     grad psi_s(y) + N_B(y), which is what ADAP-AIPP's R_j needs.
     Reading: more than max_fista iterations count as failure.
+    Floating point: when the accepted y equals x_0 within rounding
+    (|y - x_0| <= ROUND_SLACK * UNIT_ROUNDOFF * |x_0|), step 4 is not taken
+    and the call succeeds: both sides of step 4's inequality are then
+    rounding-level numbers, and a "failure" decided by them would halve
+    ADAP-AIPP's lambda for nothing (it never grows back).
     """
     cnt = sub.cnt
     x0 = center
@@ -472,10 +477,13 @@ def adap_fista(sub, lam, center, mu, L0, opt, tau):
         s = (Ln - mu) * (xt - ynew)
         x = (mu * a * ynew + tk * x - a * s) / tk_new
         dy0 = float(np.sum((ynew - x0) ** 2))
-        if dy0 < opt.chi * A_new * Ln * float(np.sum((ynew - xt) ** 2)):   # step 4
+        # y equal to x_0 within rounding: x_0 is the prox point to working
+        # precision, and step 4 would compare two rounding-level numbers
+        at_x0 = dy0 <= (ROUND_SLACK * UNIT_ROUNDOFF) ** 2 * float(np.sum(x0 * x0))
+        if not at_x0 and dy0 < opt.chi * A_new * Ln * float(np.sum((ynew - xt) ** 2)):  # step 4
             cnt.fista_fail += 1
             return "failure", None, Ln, None, None
-        if math.sqrt(float(np.sum(s * s))) <= opt.sigma * math.sqrt(dy0):  # step 5
+        if at_x0 or math.sqrt(float(np.sum(s * s))) <= opt.sigma * math.sqrt(dy0):  # step 5
             gy = sub.grad(ynew)
             dpsi_y = lam * 2.0 * gy.W + (ynew - center)
             V = dpsi_y - dpsi_xt + Ln * (xt - ynew)

@@ -198,13 +198,17 @@ __global__ void k_fista_ctl(LoopCtl* Lp, const double* __restrict__ h) {
       const double A_new = L.A + L.a, tk_new = L.tk + L.a * L.mu;
       const double snorm = (L.Ln - L.mu) * sqrt(d2);
       L.Lacc = L.Ln;
-      if (dy0 < L.chi * A_new * L.Ln * d2) {                       // step 4
+      // y equal to x_0 within rounding: x_0 is the prox point to working
+      // precision and step 4 would compare rounding-level numbers (the
+      // oracle's reading); the call succeeds
+      const bool at_x0 = dy0 <= L.slack_u * L.slack_u * L.nrm_ctr2;
+      if (!at_x0 && dy0 < L.chi * A_new * L.Ln * d2) {            // step 4
         L.fista_status = kFistaFailure;
         L.n_fista_fail++;
         if (L.verbose >= 3)
           printf("[fista4] it=%d lam=%.6e dy0=%.9e A=%.9e Ln=%.9e d2=%.9e\n", L.fista_it,
                  L.lam, dy0, A_new, L.Ln, d2);
-      } else if (snorm <= L.sigma * sqrt(dy0)) {                   // step 5
+      } else if (at_x0 || snorm <= L.sigma * sqrt(dy0)) {         // step 5
         L.fista_status = kFistaSuccess;
       } else if (L.fista_it + 1 >= L.max_fista) {
         L.fista_status = kFistaFailure;

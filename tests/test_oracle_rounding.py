@@ -205,3 +205,25 @@ def test_stalled_fires_exactly_on_a_bit_identical_prox_step():
 def test_allowance_constants():
     # the documented reading: 16 units of the FP64 roundoff
     assert O.ROUND_SLACK == 16.0 and O.UNIT_ROUNDOFF == 2.0 ** -53
+
+
+def test_fista_at_the_prox_point_succeeds_within_rounding(monkeypatch):
+    # theta(Q_6) at U ~ 1 (|U| = 1 = tau) with p = 0, beta = 1: the centre is
+    # the prox point (the gradient is radial and the ball projection undoes
+    # the step), so every ADAP-FISTA iterate equals x_0 up to rounding and
+    # step 4's inequality compares rounding-level numbers.  Reading: such a
+    # call succeeds with y = x_0 (to rounding); without the rounding
+    # allowance this case's step 4 reports a failure that would halve
+    # ADAP-AIPP's lambda
+    inst = I.theta(64, *I.hypercube_graph(6))
+    W0 = np.ones((64, 2)) / math.sqrt(128)
+
+    def run():
+        sub = O._Subproblem(inst, np.zeros(inst.m), 1.0, O.Counters())
+        return O.adap_fista(sub, 1.0, W0, 0.5, 1.0, O.Options(), 1.0)
+
+    st, y, L, V, dg = run()
+    assert st == "success"
+    assert np.linalg.norm(y - W0) <= O.ROUND_SLACK * O.UNIT_ROUNDOFF * np.linalg.norm(W0)
+    monkeypatch.setattr(O, "ROUND_SLACK", 0.0)
+    assert run()[0] == "failure"
