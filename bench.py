@@ -953,7 +953,17 @@ def main():
     if args.impl == "reference":
         line = run_reference(args, world, rank)
     else:
-        line = run_ours(args, world, rank)
+        from paper_2505_13719_b300 import hallar as H
+        try:
+            line = run_ours(args, world, rank)
+        except H.HallarError as e:
+            # a solve that stopped with an error is a result too: say which
+            if rank == 0:
+                print(json.dumps({"metric": METRIC, "value": None, "unit": "s",
+                                  "workload": WORKLOADS[args.workload]["desc"],
+                                  "precision": args.precision, "error": str(e),
+                                  "status": int(e.status)}), flush=True)
+            sys.exit(1)
     if rank == 0 and line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
