@@ -135,6 +135,8 @@ STORED = {
 # wall-clock limit per stored case: theta on a random graph takes the method
 # millions of ADAP-FISTA trials (the oracle needs about 2.8e6 gradients)
 STORED_TIME_LIMIT = {"theta_gnm_n40_m80": 600.0}
+# the mixed theta case is an expected failure (below): a shorter limit
+STORED_TIME_LIMIT_MIXED = {"theta_gnm_n40_m80": 120.0}
 
 
 # A mixed solve whose float factor stalls goes on in FP64 (options.promote,
@@ -160,7 +162,8 @@ def test_against_stored_oracle_solve(H, name, prec, request):
     tol = STORED_MIXED_TOL.get(name) if prec == 1 else None
     st, res, U, p = gpu_solve(H, inst, ref["r0"], ref["u0_seed"], prec=prec, tol=tol,
                               r_cap=ref["r_cap"],
-                              time_limit_s=STORED_TIME_LIMIT.get(name, 60.0))
+                              time_limit_s=(STORED_TIME_LIMIT_MIXED if prec == 1
+                                            else STORED_TIME_LIMIT).get(name, 60.0))
     assert st == H.HALLAR_OK, res.as_dict()
     assert abs(res.pval - ref["pval"]) <= 1e-5 * abs(ref["pval"]), (res.pval, ref["pval"])
     if not (prec == 1 and name in MIXED_MAY_PROMOTE):
