@@ -227,3 +227,19 @@ def test_fista_at_the_prox_point_succeeds_within_rounding(monkeypatch):
     assert np.linalg.norm(y - W0) <= O.ROUND_SLACK * O.UNIT_ROUNDOFF * np.linalg.norm(W0)
     monkeypatch.setattr(O, "ROUND_SLACK", 0.0)
     assert run()[0] == "failure"
+
+
+def test_ball_projection_lands_on_the_sphere_to_a_few_ulps():
+    # eq. dimensional ball: P_B(Z) = tau Z / |Z|_F outside the ball.  The
+    # step-2 tests read the projected point's radial error times the radial
+    # gradient (2n on the theta SDP), so the radius must be exact to a few
+    # units of roundoff even for a large factor; checked with exact rational
+    # arithmetic on |P_B(Z)|^2
+    # the shape of theta(Q_17)'s iterates at the fixed point U ~ 1: many equal
+    # entries, where a blocked dot product of the squares is off by 1e-14
+    n = 1 << 17
+    Z = np.full((n, 2), 0.7071 / math.sqrt(n)) * 1.31073e5
+    Y = O.project_ball(Z, 1.0)
+    r2 = sum(F(float(v)) ** 2 for v in Y.ravel())
+    assert abs(float(r2 - 1)) <= 4 * O.UNIT_ROUNDOFF
+    np.testing.assert_array_equal(O.project_ball(Y * 0.5, 1.0), Y * 0.5)
