@@ -30,7 +30,9 @@ invariants; ADAP-FISTA against the closed-form prox point of a quadratic;
 the KKT measures at a closed-form optimal primal-dual pair; full solves
 against closed-form SDP values with a dense dual certificate;
 ``splitmix64_uniform`` against the generator's published output words from
-state 0.  Parity unpinned: iteration counts and trajectories (they
+state 0; general problems in HSLR form (sparse plus low-rank A_l, Section
+3.2) against dense brute force and theta(C_5) with a low-rank cost
+(tests/test_oracle_hslr.py).  Parity unpinned: iteration counts and trajectories (they
 follow the readings, not the paper).
 """
 from __future__ import annotations
@@ -54,9 +56,13 @@ def constraint_entries(inst):
     diag  A_i = e_i e_i^T                       (one entry per constraint)
     edge  A_l = (e_i e_j^T + e_j e_i^T) / 2     (two entries, 1/2 each)
     trace A = I                                 (last constraint, n entries)
-    For ``observed`` the pair is (i, n1 + j).
+    For ``observed`` the pair is (i, n1 + j).  For ``hslr`` (eq.
+    HSLR-rep-body) the sparse parts A_l^sp as given; their low-rank parts
+    K_l D_l K_l^T are evaluated separately (``_lr_values``).
     """
     n = inst.n
+    if inst.family == "hslr":
+        return inst.sp_cons
     if inst.family == "diag":
         idx = np.arange(n, dtype=np.int64)
         return idx, idx, idx, np.ones(n)
@@ -97,6 +103,17 @@ def _pair_dots(U, a, b, chunk=1 << 20):
     return out
 
 
+def _lr_values(inst, U):
+    """A_l^lr . UU^T = tr(D_l Y_l Y_l^T) with Y_l = K_l^T U for every low-rank
+    term (Section 4.1, Alg. 3, written by definition); returns (l, value)
+    pairs, l = 0 for C."""
+    out = []
+    for l, K, D in inst.lr_terms:
+        Y = K.T @ U
+        out.append((l, float(np.sum(D * (Y @ Y.T)))))
+    return out
+
+
 # ----------------------------------------------------------------------------
 # operators (Section 4)
 # ----------------------------------------------------------------------------
@@ -112,6 +129,9 @@ def cost_dot(inst, U):
         val += inst.C_J * float(s @ s)
     if inst.C_I != 0.0:
         val += inst.C_I * float(np.sum(U * U))
+    for l, t in _lr_values(inst, U):
+        if l == 0:
+            val += t
     return val
 
 
@@ -119,7 +139,11 @@ def constraint_map(inst, U):
     """A(UU^T): T_l = sum_{(a,b) in supp A_l} (A_l)_ab <U_a, U_b>
     (Section 4.1; the sum that Alg. 2 evaluates, written by definition)."""
     ell, a, b, v = constraint_entries(inst)
-    return np.bincount(ell, weights=v * _pair_dots(U, a, b), minlength=inst.m)
+    T = np.bincount(ell, weights=v * _pair_dots(U, a, b), minlength=inst.m)
+    for l, t in _lr_values(inst, U):
+        if l > 0:
+            T[l - 1] += t
+    return T
 
 
 def eval_A_tilde(inst, U):
@@ -131,7 +155,9 @@ def adjoint_matrix(inst, ptilde):
     """M = A~*(p~) = p~_0 C_sparse + sum_l p_l A_l as a sparse matrix
     (eq. Adjoint calculation; Alg. 4 forms M on the merged pattern).  The
     implicit C_J 11^T and C_I I parts are returned separately as scaled
-    coefficients because 11^T is dense."""
+    coefficients because 11^T is dense; the low-rank parts K_l D_l K_l^T of
+    an ``hslr`` problem are not in M (``adjoint_apply`` applies them,
+    ``dense_adjoint`` forms them)."""
     ptilde = np.asarray(ptilde, dtype=np.float64)
     ell, a, b, v = constraint_entries(inst)
     ca, cb, cv = cost_entries(inst)
@@ -151,7 +177,21 @@ def adjoint_apply(inst, ptilde, U):
         W = W + cj * np.ones((inst.n, 1)) * U2.sum(axis=0, keepdims=True)
     if ci != 0.0:
         W = W + ci * U2
+    for l, K, D in inst.lr_terms:  # Alg. 5: + p~_l K_l (D_l (K_l^T U))
+        if ptilde[l] != 0.0:
+            W = W + ptilde[l] * (K @ (D @ (K.T @ U2)))
     return W if U.ndim == 2 else W[:, 0]
+
+
+def dense_adjoint(inst, ptilde):
+    """A~*(p~) = sum_l p~_l A_l as a dense n x n array, low-rank parts
+    included (small instances: certificates and brute-force pins)."""
+    ptilde = np.asarray(ptilde, dtype=np.float64)
+    M, cj, ci = adjoint_matrix(inst, ptilde)
+    G = M.toarray() + cj * np.ones((inst.n, inst.n)) + ci * np.eye(inst.n)
+    for l, K, D in inst.lr_terms:
+        G = G + ptilde[l] * (K @ D @ K.T)
+    return G
 
 
 @dataclass
@@ -190,6 +230,10 @@ def _magnitude(inst, U, ps, T):
         mag += abs(inst.C_J) * float(s @ s)
     if inst.C_I != 0.0:
         mag += abs(inst.C_I) * float(np.sum(U * U))
+    for l, K, D in inst.lr_terms:
+        if l == 0:
+            Y = K.T @ U
+            mag += float(np.sum(np.abs(D) * np.abs(Y @ Y.T)))
     return mag
 
 
@@ -243,6 +287,16 @@ def al_value_change(inst, X, Y, p, beta, rX=None):
         dT0 += inst.C_J * float(sd @ (Y.sum(axis=0) + X.sum(axis=0)))
     if inst.C_I != 0.0:
         dT0 += inst.C_I * float(np.sum(D * (Y + X)))
+    for l, K, Dl in inst.lr_terms:
+        # tr(D_l (Q Q^T - P P^T)) = tr(D_l (Delta Q^T + P Delta^T)),
+        # P = K^T X, Q = K^T Y, Delta = K^T D (no cancellation)
+        P = K.T @ X
+        Dlt = K.T @ D
+        ch = float(np.sum(Dl * (Dlt @ (P + Dlt).T + P @ Dlt.T)))
+        if l == 0:
+            dT0 += ch
+        else:
+            dT[l - 1] += ch
     if rX is None:
         rX = constraint_map(inst, X) - inst.b
     dg = dT0 + float(p @ dT) + 0.5 * beta * float(dT @ (2.0 * rX + dT))
@@ -606,6 +660,13 @@ def c_norm1(inst):
     column sum).  Reading: eq. termination2's ||C||_1 is taken as the
     induced norm."""
     n = inst.n
+    if any(l == 0 for l, _K, _D in inst.lr_terms):
+        # a low-rank part in C: the induced norm of the dense matrix
+        # (small problems only: n^2 entries)
+        if n > 20000:
+            raise ValueError("||C||_1 with a low-rank C is formed densely: n too large")
+        G = dense_adjoint(inst, np.concatenate([[1.0], np.zeros(inst.m)]))
+        return float(np.abs(G).sum(axis=0).max()) if n else 0.0
     a, b, v = cost_entries(inst)
     M = sp.coo_matrix((v, (a, b)), shape=(n, n)).tocsc()
     M.sum_duplicates()

@@ -23,6 +23,17 @@ HALLAR_DIAG, HALLAR_EDGE, HALLAR_OBSERVED = 0, 1, 2
 HALLAR_FP64, HALLAR_MIXED = 0, 1
 FAMILY = {"diag": HALLAR_DIAG, "edge": HALLAR_EDGE, "observed": HALLAR_OBSERVED}
 
+
+def _family_code(family):
+    """hallar_family of a family name; general HSLR problems (family
+    "hslr") have no device kernels yet and are refused here."""
+    if not isinstance(family, str):
+        return int(family)
+    if family not in FAMILY:
+        raise ValueError(f"family {family!r}: the device library implements "
+                         f"{', '.join(FAMILY)} only")
+    return FAMILY[family]
+
 EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_grad",
             "hallar_value_change", "hallar_trim_rank", "hallar_maxcut_round",
             "hallar_factor_entries", "hallar_min_eig", "hallar_solve", "hallar_get_solution", "hallar_get_sizes",
@@ -178,7 +189,7 @@ def hallar_default_options(**overrides) -> hallar_options:
 def hallar_create(n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, cons_i, cons_j,
                   has_trace_row, b, tau2, opt: hallar_options | None = None):
     """Create a handle from host arrays (see hallar_create in hallar.h)."""
-    fam = FAMILY[family] if isinstance(family, str) else int(family)
+    fam = _family_code(family)
     rp = None if C_rowptr is None else np.ascontiguousarray(C_rowptr, dtype=np.int64)
     ci = np.ascontiguousarray([] if C_col is None else C_col, dtype=np.int32)
     cv = np.ascontiguousarray([] if C_val is None else C_val, dtype=np.float64)
@@ -198,7 +209,7 @@ def hallar_create(n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, cons_i, cons_
 def hallar_check_problem(n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, cons_i, cons_j,
                          has_trace_row, b, tau2):
     """Host-only validation and merge (see hallar.h): (m, nnz_merged, c_norm1)."""
-    fam = FAMILY[family] if isinstance(family, str) else int(family)
+    fam = _family_code(family)
     rp = None if C_rowptr is None else np.ascontiguousarray(C_rowptr, dtype=np.int64)
     ci = np.ascontiguousarray([] if C_col is None else C_col, dtype=np.int32)
     cv = np.ascontiguousarray([] if C_val is None else C_val, dtype=np.float64)
@@ -386,7 +397,7 @@ def request_from_instance(inst, U0, precision=HALLAR_FP64, **options):
     Returns (request, keep): `keep` holds the arrays the request points to;
     it must stay alive until hallar_server_submit returns."""
     opt = hallar_default_options(precision=precision, **options)
-    fam = FAMILY[inst.family] if isinstance(inst.family, str) else int(inst.family)
+    fam = _family_code(inst.family)
     dt = np.float32 if precision == HALLAR_MIXED else np.float64
     keep = {
         "rp": None if inst.C_rowptr is None else np.ascontiguousarray(inst.C_rowptr, np.int64),

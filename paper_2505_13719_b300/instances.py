@@ -28,6 +28,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 FAMILIES = ("diag", "edge", "observed")
+# general problems in HSLR form (Section 3.2, eq. HSLR-rep-body); the oracle
+# evaluates them, the device library has no kernels for them yet
+GENERAL_FAMILIES = ("hslr",)
 
 
 @dataclass
@@ -59,6 +62,11 @@ class Instance:
     tau2: float
     sense: float = 1.0
     meta: dict = field(default_factory=dict)
+    # family "hslr" only: the sparse parts of A_1..A_m as entries (l, a, b, v)
+    # over the full symmetric pattern (both triangles, l zero-based), and the
+    # low-rank parts as (l, K_l, D_l) with l = 0 for C
+    sp_cons: tuple | None = None
+    lr_terms: list = field(default_factory=list)
 
     @property
     def m(self) -> int:
@@ -315,3 +323,70 @@ def theta_gnm(n: int = 100_000, M: int = 1_000_000, seed: int = 3) -> Instance:
     """Lovasz theta SDP on G(n, M) with the tr X = 1 row."""
     ei, ej = gnm_graph(n, M, seed)
     return theta(n, ei, ej, trace_row=True, name=f"theta_gnm_n{n}_m{M}")
+
+
+# ----------------------------------------------------------------------------
+# general problems in HSLR form
+# ----------------------------------------------------------------------------
+
+def _upper_to_full(ell, a, b, v):
+    """Entries of symmetric matrices listed by their upper triangle (a <= b)
+    -> the full pattern (both triangles; the diagonal once)."""
+    ell = np.asarray(ell, dtype=np.int64)
+    a = np.asarray(a, dtype=np.int64)
+    b = np.asarray(b, dtype=np.int64)
+    v = np.asarray(v, dtype=np.float64)
+    if np.any(a > b):
+        raise ValueError("entries must be listed by their upper triangle (i <= j)")
+    off = a != b
+    return (np.concatenate([ell, ell[off]]), np.concatenate([a, b[off]]),
+            np.concatenate([b, a[off]]), np.concatenate([v, v[off]]))
+
+
+def hslr(n: int, sp_upper, lr_terms, b, tau2: float, sense: float = 1.0,
+         name: str = "hslr", meta: dict | None = None) -> Instance:
+    """A general SDP (P) in Hybrid Sparse Low-Rank form (Section 3.2, eq.
+    HSLR-rep-body): A_l = A_l^sp + K_l D_l K_l^T for l = 0..m, C = A_0.
+
+    sp_upper: (l, i, j, v) arrays, the nonzero entries of every A_l^sp on or
+        above the diagonal (i <= j), l = 0 for C and 1..m for the constraints.
+    lr_terms: a list of (l, K_l, D_l): K_l an n x r_l array, D_l an r_l x r_l
+        symmetric array (not necessarily diagonal).
+    b: the m right-hand sides; tau2 the trace bound tau^2 of the spectraplex.
+    Duplicate (l, i, j) entries are summed.
+    """
+    ell, a, bb, v = (np.asarray(x) for x in sp_upper)
+    b = np.asarray(b, dtype=np.float64)
+    m = b.shape[0]
+    if ell.size and (ell.min() < 0 or ell.max() > m):
+        raise ValueError("matrix index outside 0..m")
+    if a.size and (min(a.min(), bb.min()) < 0 or max(a.max(), bb.max()) >= n):
+        raise ValueError("entry index outside 0..n-1")
+    terms = []
+    for l, K, D in lr_terms:
+        K = np.asarray(K, dtype=np.float64)
+        D = np.asarray(D, dtype=np.float64)
+        if K.ndim == 1:
+            K = K[:, None]
+        D = np.atleast_2d(D)
+        if not (0 <= l <= m) or K.shape[0] != n or D.shape != (K.shape[1], K.shape[1]):
+            raise ValueError("low-rank term shape")
+        if not np.allclose(D, D.T, rtol=0.0, atol=0.0):
+            raise ValueError("D_l must be symmetric")
+        terms.append((int(l), K, D))
+    c0 = ell == 0
+    ci, cj, cv = a[c0].astype(np.int64), bb[c0].astype(np.int64), v[c0].astype(np.float64)
+    if np.any(ci > cj):
+        raise ValueError("entries must be listed by their upper triangle (i <= j)")
+    off = ci != cj
+    diag = np.zeros(n)
+    np.add.at(diag, ci[~off], cv[~off])
+    rowptr, col, val = _sym_csr(n, ci[off], cj[off], cv[off], diag=diag)
+    # duplicates of one (i, j) in C: _sym_csr keeps them as separate stored
+    # entries, which the entry sums treat as their sum
+    cons = _upper_to_full(ell[~c0] - 1, a[~c0], bb[~c0], v[~c0])
+    return Instance(name=name, family="hslr", n=n, n1=0, C_rowptr=rowptr, C_col=col,
+                    C_val=val, C_J=0.0, C_I=0.0, cons_i=np.zeros(0, np.int32),
+                    cons_j=np.zeros(0, np.int32), has_trace_row=False, b=b,
+                    tau2=float(tau2), sense=float(sense), meta=dict(meta or {}),
+                    sp_cons=cons, lr_terms=terms)
