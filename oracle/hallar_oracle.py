@@ -32,7 +32,9 @@ against closed-form SDP values with a dense dual certificate;
 ``splitmix64_uniform`` against the generator's published output words from
 state 0; general problems in HSLR form (sparse plus low-rank A_l, Section
 3.2) against dense brute force and theta(C_5) with a low-rank cost
-(tests/test_oracle_hslr.py).  Parity unpinned: iteration counts and trajectories (they
+(tests/test_oracle_hslr.py); phase retrieval's FFT operators against a
+brute-force DFT, its real embedding, and exact recovery of the signal
+(tests/test_oracle_phase.py).  Parity unpinned: iteration counts and trajectories (they
 follow the readings, not the paper).
 """
 from __future__ import annotations
@@ -139,7 +141,8 @@ def constraint_map(inst, U):
     """A(UU^T): T_l = sum_{(a,b) in supp A_l} (A_l)_ab <U_a, U_b>
     (Section 4.1; the sum that Alg. 2 evaluates, written by definition)."""
     ell, a, b, v = constraint_entries(inst)
-    T = np.bincount(ell, weights=v * _pair_dots(U, a, b), minlength=inst.m)
+    # (bincount of no entries is an integer array: force float)
+    T = np.bincount(ell, weights=v * _pair_dots(U, a, b), minlength=inst.m).astype(np.float64)
     for l, t in _lr_values(inst, U):
         if l > 0:
             T[l - 1] += t
@@ -279,7 +282,8 @@ def al_value_change(inst, X, Y, p, beta, rX=None):
     """
     D = Y - X
     ell, a, b, v = constraint_entries(inst)
-    dT = np.bincount(ell, weights=v * _pair_change(X, Y, D, a, b), minlength=inst.m)
+    dT = np.bincount(ell, weights=v * _pair_change(X, Y, D, a, b),
+                     minlength=inst.m).astype(np.float64)
     ca, cb, cv = cost_entries(inst)
     dT0 = float(np.dot(cv, _pair_change(X, Y, D, ca, cb))) if cv.shape[0] else 0.0
     if inst.C_J != 0.0:
@@ -306,6 +310,77 @@ def al_value_change(inst, X, Y, p, beta, rX=None):
 def gradient_matrix_apply(inst, pshift, v):
     """G v with G = C + A*(p') (eq. Grad X Space)."""
     return adjoint_apply(inst, np.concatenate([[1.0], pshift]), v)
+
+
+# ----------------------------------------------------------------------------
+# phase retrieval (Section 5.4): complex factors, FFT operators
+# ----------------------------------------------------------------------------
+
+
+def phase_map(inst, U):
+    """[A(UU^H)]_{k,j} = sum_s |FFT(d_k * U_s)_j|^2 for the coded diffraction
+    measurements a_{k,j}^H x = FFT(d_k * x)_j of a ``phase`` instance (eq.
+    phase retrieval SDP; the FFT is the only library step).  U: n x r
+    complex; returns the m = K n values, k-major."""
+    U = np.asarray(U, dtype=np.complex128)
+    U2 = U if U.ndim == 2 else U[:, None]
+    out = np.empty((inst.masks.shape[0], inst.n))
+    for k, d in enumerate(inst.masks):
+        Y = np.fft.fft(d[:, None] * U2, axis=0)
+        out[k] = np.sum(np.abs(Y) ** 2, axis=1)
+    return out.ravel()
+
+
+def phase_adjoint(inst, p, U):
+    """A*(p) U = sum_{k,j} p_{k,j} a_{k,j} a_{k,j}^H U for the same
+    measurements: sum_k conj(d_k) * F^H (p_k * F (d_k * U)), F^H y = n ifft(y)."""
+    U = np.asarray(U, dtype=np.complex128)
+    U2 = U if U.ndim == 2 else U[:, None]
+    p = np.asarray(p, dtype=np.float64).reshape(inst.masks.shape)
+    W = np.zeros_like(U2)
+    for k, d in enumerate(inst.masks):
+        Y = np.fft.fft(d[:, None] * U2, axis=0) * p[k][:, None]
+        W += np.conj(d)[:, None] * (inst.n * np.fft.ifft(Y, axis=0))
+    return W if U.ndim == 2 else W[:, 0]
+
+
+def phase_vectors(inst):
+    """The measurement vectors as an m x n array of rows a_i^H (row k n + j
+    is the j-th DFT row times diag(d_k)); small instances, brute force."""
+    n = inst.n
+    t = np.arange(n)
+    F = np.exp(-2j * np.pi * np.outer(t, t) / n)
+    return np.concatenate([F * d[None, :] for d in inst.masks])
+
+
+def embed_factor(U):
+    """The real factor of the real embedding of a complex factor:
+    [[Re U, -Im U], [Im U, Re U]] (2n x 2r), whose Gram is the real form
+    [[Re X, -Im X], [Im X, Re X]] of X = UU^H."""
+    U = np.asarray(U, dtype=np.complex128)
+    return np.block([[U.real, -U.imag], [U.imag, U.real]])
+
+
+def phase_to_hslr(inst):
+    """The phase retrieval SDP as a real SDP on 2n in HSLR form (Section 3.2).
+    A Hermitian X is psd iff its real form X_R is, tr X_R = 2 tr X, and
+    <a a^H, X> = <(v1 v1^T + v2 v2^T)/2, X_R> with v1 = [Re a; Im a],
+    v2 = [-Im a; Re a]; the J-invariant A_R keeps the real relaxation's value
+    equal to the complex one.  So C_R = I/2, A_R = K D K^T with K = [v1 v2],
+    D = I/2, b unchanged, tau_R^2 = 2 tau^2."""
+    from paper_2505_13719_b300 import instances as _I
+    n = inst.n
+    Ah = phase_vectors(inst)          # rows a^H
+    a = np.conj(Ah)                   # rows a
+    terms = []
+    for i in range(a.shape[0]):
+        v1 = np.concatenate([a[i].real, a[i].imag])
+        v2 = np.concatenate([-a[i].imag, a[i].real])
+        terms.append((i + 1, np.stack([v1, v2], axis=1), 0.5 * np.eye(2)))
+    d = np.arange(2 * n)
+    sp_upper = (np.zeros(2 * n, np.int64), d, d, np.full(2 * n, 0.5))
+    return _I.hslr(2 * n, sp_upper, terms, inst.b, 2.0 * inst.tau2, sense=1.0,
+                   name=inst.name + "_real")
 
 
 # ----------------------------------------------------------------------------

@@ -30,7 +30,7 @@ import numpy as np
 FAMILIES = ("diag", "edge", "observed")
 # general problems in HSLR form (Section 3.2, eq. HSLR-rep-body); the oracle
 # evaluates them, the device library has no kernels for them yet
-GENERAL_FAMILIES = ("hslr",)
+GENERAL_FAMILIES = ("hslr", "phase")
 
 
 @dataclass
@@ -67,6 +67,9 @@ class Instance:
     # low-rank parts as (l, K_l, D_l) with l = 0 for C
     sp_cons: tuple | None = None
     lr_terms: list = field(default_factory=list)
+    # family "phase" only: the K x n complex masks of the coded diffraction
+    # measurements (phase retrieval, Section 5.4)
+    masks: np.ndarray | None = None
 
     @property
     def m(self) -> int:
@@ -390,3 +393,31 @@ def hslr(n: int, sp_upper, lr_terms, b, tau2: float, sense: float = 1.0,
                     cons_j=np.zeros(0, np.int32), has_trace_row=False, b=b,
                     tau2=float(tau2), sense=float(sense), meta=dict(meta or {}),
                     sp_cons=cons, lr_terms=terms)
+
+
+# ----------------------------------------------------------------------------
+# phase retrieval (Section 5.4)
+# ----------------------------------------------------------------------------
+
+def phase_retrieval(n: int, K: int = 12, seed: int = 7, name: str = "phase") -> Instance:
+    """The phase retrieval SDP of Section 5.4 (eq. phase retrieval SDP):
+    min tr X s.t. <a_i a_i^H, X> = b_i, X Hermitian psd, with tau^2 = |x|^2
+    (the paper takes the squared norm of the signal as the trace bound).
+
+    Reading: the paper fixes no measurement ensemble beyond needing an FFT.
+    Here the measurements are coded diffraction patterns: K masks d_k with
+    entries drawn uniformly from {1, -1, i, -i}, and b_{k,j} = |FFT(d_k * x)_j|^2
+    for j = 0..n-1 (numpy's unnormalised forward FFT), so m = K n (the paper's
+    instances have m = 12 n).  The signal x has independent standard complex
+    Gaussian entries.  Family "phase"; C = I (C_I = 1), n complex dimensions.
+    """
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / math.sqrt(2.0)
+    masks = np.array([1.0, -1.0, 1j, -1j])[rng.integers(0, 4, size=(K, n))]
+    b = (np.abs(np.fft.fft(masks * x[None, :], axis=1)) ** 2).ravel()
+    rowptr, col, val = _empty_csr(n)
+    return Instance(name=name, family="phase", n=n, n1=0, C_rowptr=rowptr, C_col=col,
+                    C_val=val, C_J=0.0, C_I=1.0, cons_i=np.zeros(0, np.int32),
+                    cons_j=np.zeros(0, np.int32), has_trace_row=False, b=b,
+                    tau2=float(np.vdot(x, x).real), sense=1.0,
+                    meta={"signal": x, "K": K}, masks=masks)
