@@ -427,7 +427,18 @@ def run_hypercube(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st, res = H.hallar_solve(hd.h, U0, 2)
+        try:
+            st, res = H.hallar_solve(hd.h, U0, 2)
+        except H.HallarError as e:
+            # a solver error is this row's result; the sweep goes on
+            e1.record(stream)
+            e1.synchronize()
+            hd.close()
+            rows.append({"d": d, "n": inst.n, "edges": int(inst.meta["edges"]),
+                         "time_s": round(e0.elapsed_time(e1) / 1e3, 4), "status": int(e.status),
+                         "error": str(e)})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            continue
         e1.record(stream)
         e1.synchronize()
         hd.close()
