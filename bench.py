@@ -558,7 +558,8 @@ def run_ours(args, world, rank):
     dt = np.float32 if prec == H.HALLAR_MIXED else np.float64
     U0h = I.initial_factor(inst.n, wl["r0"], wl["u0_seed"]).astype(dt)
     stream = torch.cuda.current_stream()
-    opts = dict(tol=TOL, r_cap=wl["r_cap"], time_limit_s=args.time_limit, stream=stream.cuda_stream)
+    opts = dict(tol=TOL, r_cap=wl["r_cap"], time_limit_s=args.time_limit, stream=stream.cuda_stream,
+                lambda_kappa=args.lambda_kappa)
     hd = H.create_from_instance(inst, prec, **opts)
     U0 = torch.from_numpy(U0h).cuda()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -726,7 +727,8 @@ def run_ours(args, world, rank):
         "config": {"workload": wl["desc"], "precision": args.precision, "tol": TOL,
                    "r0": wl["r0"], "r_cap": wl["r_cap"], "n": inst.n, "m": inst.m,
                    "parallelism": f"replicas{world}",
-                   "l2": "flushed between timed solves (256 MB write)"},
+                   "l2": "flushed between timed solves (256 MB write)",
+                   **({"lambda_kappa": args.lambda_kappa} if args.lambda_kappa > 0 else {})},
         "solves_per_s": round(world * args.steps / wall, 5),
         "p50_s": round(statistics.median(times), 4),
         "p99_s": round(float(np.percentile(times, 99)), 4),
@@ -915,6 +917,9 @@ def main():
                     help="default: the workload's own (FP64 for the ER configuration, "
                          "mixed for the others)")
     ap.add_argument("--time-limit", type=float, default=600.0)
+    ap.add_argument("--lambda-kappa", type=float, default=0.0,
+                    help="> 0: every ADAP-AIPP call starts at lambda = K / beta_t "
+                         "(hallar_options.lambda_kappa); 0: the carried lambda")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true",

@@ -102,6 +102,10 @@ typedef struct {
   double eps1_rel;        /* epsilon_1 = eps1_rel (1 + tau^2 ||C||_1) (1e-2)      */
   double lanczos_tol_rel; /* Ritz residual tol = this * epsilon_t / tau^2 (0.5)   */
   double time_limit_s;    /* wall-clock limit of hallar_solve (3600)              */
+  double lambda_kappa;    /* > 0: every ADAP-AIPP call starts at the prox stepsize
+                           * lambda_kappa / beta_t (the subproblem's curvature grows
+                           * with the penalty); 0: lambda starts at lambda0 and is
+                           * carried over between calls (0)                       */
   int32_t r_cap;          /* maximum factor rank; the Gram trim keeps r_cap (32)  */
   int32_t max_outer;      /* AL iterations (300)                                  */
   int32_t max_hlr;        /* HLR iterations per AL iteration (100)                */

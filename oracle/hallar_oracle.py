@@ -503,6 +503,9 @@ class Options:
     sigma: float = 0.3
     chi: float = 0.5
     lambda0: float = 1.0
+    # > 0: every ADAP-AIPP call starts at lambda_kappa / beta_t instead of
+    # the carried lambda (0: carried, the default reading)
+    lambda_kappa: float = 0.0
     beta0: float = 1.0
     beta_max: float = 1e8
     eps_decay: float = 0.5
@@ -821,6 +824,8 @@ def hallar_solve(inst, U0, p0=None, opt: Options | None = None, log=None):
         Yt = U
         for _h in range(opt.max_hlr):                                   # HLR
             cnt.hlr_iters += 1
+            if opt.lambda_kappa > 0.0:
+                aipp.lam = opt.lambda_kappa / beta
             Y, _R = adap_aipp(sub, Yt, rho_t, aipp, opt, tau)      # step 6
             gr = al_grad(inst, Y, p, beta)                               # step 7
             GdotX = float(np.sum(gr.W * Y))

@@ -454,6 +454,7 @@ hallar_status hallar_default_options(hallar_options* o) {
   o->eps1_rel = 1e-2;
   o->lanczos_tol_rel = 0.5;
   o->time_limit_s = 3600.0;
+  o->lambda_kappa = 0.0;
   o->r_cap = 32;
   o->max_outer = 300;
   o->max_hlr = 100;
@@ -493,7 +494,8 @@ hallar_status hallar_create(int64_t n, int64_t n1, const int64_t* C_rowptr, cons
         !(o.eps_decay > 0.0 && o.eps_decay <= 1.0) || !(o.eps1_rel > 0.0) ||
         !(o.lanczos_tol_rel > 0.0) || !(o.time_limit_s > 0.0) || o.max_fista < 1 ||
         o.max_aipp < 1 || o.max_outer < 1 || o.max_hlr < 1 || o.lanczos_kmax < 2 ||
-        (o.promote != 0 && o.promote != 1))
+        (o.promote != 0 && o.promote != 1) || !(o.lambda_kappa >= 0.0) ||
+        !std::isfinite(o.lambda_kappa))
       fail(HALLAR_EINVAL, "invalid options");
     HL_CUDA(cudaGetDevice(&c->device));
     HL_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));

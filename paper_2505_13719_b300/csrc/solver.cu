@@ -15,7 +15,8 @@
 //     eps_1 = eps1_rel (1 + tau^2 ||C||_1); ADAP-AIPP gets rho = epsilon_t / tau;
 //   * beta doubles (<= beta_max (1 + ||C||_1)) when ||r_t|| > ||r_{t-1}|| / 4
 //     while the relative primal infeasibility is above tol;
-//   * ADAP-AIPP: M_j = max(1, Mbar_{j-1}/2), lambda carried across calls;
+//   * ADAP-AIPP: M_j = max(1, Mbar_{j-1}/2), lambda carried across calls
+//     (options.lambda_kappa > 0: each call starts at lambda_kappa / beta_t);
 //   * ADAP-FISTA: linearisation test with g(y) - g(x~) formed as a
 //     difference; V = grad psi(y) - grad psi(x~) + L (x~ - y);
 //   * floating point: the step-2 tests of ADAP-FISTA and ADAP-AIPP accept a
@@ -333,6 +334,7 @@ struct Solver {
     grad_enqueue(Y(), nullptr, rpool[ir]);
     fetch();
     const double nrm_ctr2 = c->h_scal[S_PRE];
+    if (o.lambda_kappa > 0.0) lam = o.lambda_kappa / beta;  // a fresh start per call
     const bool eager = c->prof_on;  // per-kernel timing needs launches of their own
     LoopCtl& H = *h_ctl;
     std::memset(&H, 0, sizeof(LoopCtl));

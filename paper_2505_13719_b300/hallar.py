@@ -50,6 +50,7 @@ class hallar_options(C.Structure):
                 ("lambda0", C.c_double), ("beta0", C.c_double), ("beta_max", C.c_double),
                 ("eps_decay", C.c_double), ("eps1_rel", C.c_double),
                 ("lanczos_tol_rel", C.c_double), ("time_limit_s", C.c_double),
+                ("lambda_kappa", C.c_double),
                 ("r_cap", C.c_int32), ("max_outer", C.c_int32), ("max_hlr", C.c_int32),
                 ("max_aipp", C.c_int32), ("max_fista", C.c_int32),
                 ("lanczos_kmax", C.c_int32), ("precision", C.c_int32),

@@ -253,3 +253,14 @@ def test_penalty_cap_scales_with_the_cost_norm():
     assert max(betas) == 65.0
     assert betas[:8] == sorted(betas[:8])
     assert all(b == 65.0 or b == 2.0 ** round(math.log2(b)) for b in betas)
+
+
+def test_lambda_restart_option_reaches_the_closed_form():
+    # options.lambda_kappa > 0: every ADAP-AIPP call starts at lambda_kappa /
+    # beta_t instead of the carried lambda; a schedule choice, so the solve
+    # must still reach theta(C_9) = 9 cos(pi/9) / (1 + cos(pi/9))
+    inst = I.theta(9, *I.cycle_graph(9))
+    ref = 9 * math.cos(math.pi / 9) / (1 + math.cos(math.pi / 9))
+    res = O.hallar_solve(inst, I.initial_factor(9, 2, 7), opt=O.Options(tol=1e-7, lambda_kappa=100.0))
+    assert res.converged
+    assert abs(inst.sense * res.pval - ref) <= 1e-6 * ref

@@ -47,3 +47,17 @@ def test_server_options_are_validated(H):
     with pytest.raises(H.HallarError) as e:
         H.hallar_server_create(1e9, 0)
     assert e.value.status == H.HALLAR_EINVAL
+
+
+def test_options_layout_matches_the_header(H):
+    # hallar_default_options fills the struct in C; reading every field back
+    # through the ctypes mirror pins the two layouts to each other (a shifted
+    # field would misread all that follow it)
+    o = H.hallar_default_options()
+    want = dict(tol=1e-5, sigma=0.3, chi=0.5, lambda0=1.0, beta0=1.0, beta_max=1e8,
+                eps_decay=0.5, eps1_rel=1e-2, lanczos_tol_rel=0.5, time_limit_s=3600.0,
+                lambda_kappa=0.0, r_cap=32, max_outer=300, max_hlr=100, max_aipp=20000,
+                max_fista=400, lanczos_kmax=300, precision=0, verbose=0, promote=1, seed=0)
+    for k, v in want.items():
+        assert getattr(o, k) == v, k
+    assert o.stream is None
