@@ -499,6 +499,27 @@ hallar_status hallar_check_problem(int64_t n, int64_t n1, const int64_t* C_rowpt
                                    int32_t has_trace_row, const double* b, double tau2,
                                    int64_t* m, int64_t* nnz_merged, double* c_norm1);
 
+/* Merged support of general sparse data matrices (Section 4.1, eqs.
+ * support S ell and index list; the pattern S and lists L_ij that Alg. 4
+ * forms M from): the host half of general HSLR/SDPA input (Section 3.2).
+ *   n          order of the matrices (> 0); m: constraints (>= 0).
+ *   count      listed entries; ell[k] in 0..m (0 = C), 0 <= ii[k] <= jj[k] < n
+ *              (each symmetric matrix by its upper triangle), val[k] finite.
+ *              Entries repeated for one (l, i, j) are summed; entries that are
+ *              or sum to exactly 0 are dropped.
+ * Outputs (host, written when non-NULL; call once with NULL arrays for the
+ * sizes): *nnz_S stored pattern entries (both triangles: the diagonal once,
+ * every off-diagonal pair twice), *nnz_L list entries; rowptr[n+1] and
+ * col[nnz_S] the CSR of the pattern (columns ascending); for stored entry e,
+ * its list L_ij is lidx/lval[lptr[e] .. lptr[e+1]) (lptr[nnz_S+1]), matrices
+ * ascending, so M_ij = sum over the list of p~[lidx] * lval.
+ * Host arithmetic only.  Errors: HALLAR_EINVAL (reason in
+ * hallar_last_error(NULL)), HALLAR_ENOMEM. */
+hallar_status hallar_merge_general(int64_t n, int64_t m, int64_t count, const int32_t* ell,
+                                   const int32_t* ii, const int32_t* jj, const double* val,
+                                   int64_t* nnz_S, int64_t* nnz_L, int64_t* rowptr,
+                                   int32_t* col, int64_t* lptr, int32_t* lidx, double* lval);
+
 /* Problem sizes of a handle (host pointers; any may be NULL). */
 hallar_status hallar_get_sizes(hallar_t h, int64_t* n, int64_t* m, int64_t* nnz_merged,
                                int32_t* precision);

@@ -3,6 +3,7 @@
 // staging and the error model (a status per call, a message per handle).
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <map>
 #include <mutex>
 #include <cstring>
@@ -952,6 +953,80 @@ hallar_status hallar_check_problem(int64_t n, int64_t n1, const int64_t* C_rowpt
     if (m) *m = hp.m;
     if (nnz_merged) *nnz_merged = hp.nnz;
     if (c_norm1) *c_norm1 = hp.c_norm1;
+    return HALLAR_OK;
+  } catch (const Err& e) {
+    g_create_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    g_create_error = "host allocation failed";
+    return HALLAR_ENOMEM;
+  }
+}
+
+hallar_status hallar_merge_general(int64_t n, int64_t m, int64_t count, const int32_t* ell,
+                                   const int32_t* ii, const int32_t* jj, const double* val,
+                                   int64_t* nnz_S, int64_t* nnz_L, int64_t* rowptr,
+                                   int32_t* col, int64_t* lptr, int32_t* lidx, double* lval) {
+  g_create_error.clear();
+  try {
+    if (n <= 0 || n > INT32_MAX || m < 0 || m > INT32_MAX - 1 || count < 0)
+      fail(HALLAR_EINVAL, "need 0 < n < 2^31, 0 <= m < 2^31 - 1, count >= 0");
+    if (count > 0 && (!ell || !ii || !jj || !val)) fail(HALLAR_EINVAL, "entry arrays are NULL");
+    struct Ent {
+      int32_t i, j, l;
+      double v;
+    };
+    std::vector<Ent> es;
+    es.reserve((size_t)count * 2);
+    for (int64_t k = 0; k < count; ++k) {
+      const int32_t l = ell[k], i = ii[k], j = jj[k];
+      const double v = val[k];
+      if (l < 0 || l > m) fail(HALLAR_EINVAL, "entry " + std::to_string(k) + ": matrix index outside 0..m");
+      if (i < 0 || j >= n || i > j)
+        fail(HALLAR_EINVAL, "entry " + std::to_string(k) + ": need 0 <= i <= j < n (upper triangle)");
+      if (!std::isfinite(v)) fail(HALLAR_EINVAL, "entry " + std::to_string(k) + ": non-finite value");
+      if (v == 0.0) continue;
+      es.push_back({i, j, l, v});
+      if (i != j) es.push_back({j, i, l, v});
+    }
+    std::sort(es.begin(), es.end(), [](const Ent& a, const Ent& b) {
+      if (a.i != b.i) return a.i < b.i;
+      if (a.j != b.j) return a.j < b.j;
+      return a.l < b.l;
+    });
+    // sum repeats of one (i, j, l) in order, drop exact zeros
+    std::vector<Ent> mg;
+    mg.reserve(es.size());
+    for (size_t k = 0; k < es.size();) {
+      Ent e = es[k];
+      size_t q = k + 1;
+      while (q < es.size() && es[q].i == e.i && es[q].j == e.j && es[q].l == e.l) e.v += es[q++].v;
+      if (e.v != 0.0) mg.push_back(e);
+      k = q;
+    }
+    int64_t s = 0;
+    for (size_t k = 0; k < mg.size(); ++k)
+      if (k == 0 || mg[k].i != mg[k - 1].i || mg[k].j != mg[k - 1].j) ++s;
+    if (nnz_S) *nnz_S = s;
+    if (nnz_L) *nnz_L = (int64_t)mg.size();
+    if (rowptr || col || lptr || lidx || lval) {
+      if (!rowptr || !col || !lptr || !lidx || !lval)
+        fail(HALLAR_EINVAL, "the output arrays are all NULL (sizes) or all given");
+      std::fill(rowptr, rowptr + n + 1, (int64_t)0);
+      int64_t e = -1;
+      for (size_t k = 0; k < mg.size(); ++k) {
+        if (k == 0 || mg[k].i != mg[k - 1].i || mg[k].j != mg[k - 1].j) {
+          ++e;
+          col[e] = mg[k].j;
+          lptr[e] = (int64_t)k;
+          rowptr[mg[k].i + 1]++;
+        }
+        lidx[k] = mg[k].l;
+        lval[k] = mg[k].v;
+      }
+      lptr[s] = (int64_t)mg.size();
+      for (int64_t r = 0; r < n; ++r) rowptr[r + 1] += rowptr[r];
+    }
     return HALLAR_OK;
   } catch (const Err& e) {
     g_create_error = e.msg;

@@ -42,7 +42,8 @@ EXPORTED = ("hallar_default_options", "hallar_create", "hallar_eval_A", "hallar_
             "hallar_server_submit", "hallar_server_wait", "hallar_server_get_stats",
             "hallar_server_destroy", "hallar_server_last_error", "hallar_batch_create",
             "hallar_batch_layout", "hallar_batch_grad", "hallar_batch_shape",
-            "hallar_batch_destroy", "hallar_batch_last_error", "hallar_check_problem")
+            "hallar_batch_destroy", "hallar_batch_last_error", "hallar_check_problem",
+            "hallar_merge_general")
 
 
 class hallar_options(C.Structure):
@@ -130,6 +131,7 @@ def _load():
         "hallar_server_get_stats": ([P, P], C.c_int),
         "hallar_server_destroy": ([P], None),
         "hallar_server_last_error": ([P], C.c_char_p),
+        "hallar_merge_general": ([I64, I64, I64, P, P, P, P, P, P, P, P, P, P, P], I32),
         "hallar_check_problem": ([I64, I64, P, P, P, D, D, I32, I64, P, P, I32, P, D, P, P, P],
                                  C.c_int),
         "hallar_batch_create": ([I32, P, I32, I32, P, C.POINTER(C.c_void_p)], C.c_int),
@@ -225,6 +227,37 @@ def hallar_check_problem(n, n1, C_rowptr, C_col, C_val, C_J, C_I, family, cons_i
                                    C.byref(m), C.byref(nnz), C.byref(cn))
     _check(st, None)
     return m.value, nnz.value, cn.value
+
+
+def hallar_merge_general(n, m, ell, ii, jj, val):
+    """Merged support of general sparse data matrices (see hallar.h):
+    (rowptr, col, lptr, lidx, lval), the pattern S as CSR over both triangles
+    and, per stored entry, its list L_ij of (matrix, value).  Entries are
+    (ell, ii, jj, val) with ii <= jj (upper triangles), ell = 0 for C."""
+    el = np.ascontiguousarray(ell, dtype=np.int32)
+    ia = np.ascontiguousarray(ii, dtype=np.int32)
+    ja = np.ascontiguousarray(jj, dtype=np.int32)
+    va = np.ascontiguousarray(val, dtype=np.float64)
+    k = int(el.shape[0])
+    if not (ia.shape[0] == ja.shape[0] == va.shape[0] == k):
+        raise ValueError("entry arrays differ in length")
+    ns, nl = C.c_int64(), C.c_int64()
+    st = _lib.hallar_merge_general(int(n), int(m), k, _ptr(el), _ptr(ia), _ptr(ja), _ptr(va),
+                                   C.byref(ns), C.byref(nl), None, None, None, None, None)
+    _check(st, None)
+    if ns.value == 0:  # nothing stored: the empty pattern
+        return (np.zeros(int(n) + 1, dtype=np.int64), np.zeros(0, np.int32),
+                np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float64))
+    rowptr = np.empty(int(n) + 1, dtype=np.int64)
+    col = np.empty(ns.value, dtype=np.int32)
+    lptr = np.empty(ns.value + 1, dtype=np.int64)
+    lidx = np.empty(nl.value, dtype=np.int32)
+    lval = np.empty(nl.value, dtype=np.float64)
+    st = _lib.hallar_merge_general(int(n), int(m), k, _ptr(el), _ptr(ia), _ptr(ja), _ptr(va),
+                                   None, None, _ptr(rowptr), _ptr(col), _ptr(lptr), _ptr(lidx),
+                                   _ptr(lval))
+    _check(st, None)
+    return rowptr, col, lptr, lidx, lval
 
 
 def check_instance(inst):
